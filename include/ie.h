@@ -1,0 +1,177 @@
+/*
+ * ie.h -- C ABI of the GB300 interior eigensolver built on the composite-rule
+ * rational filter of Chen & Li, "Interior Eigensolver Based on Rational Filter
+ * with Composite Rule" (arXiv 2310.18043).
+ *
+ * Problem (Sec. 1, Eq. problem): all eigenpairs A x = lambda B x with lambda in
+ * the disk D = { |z - center| < radius } of a sparse non-Hermitian pencil (A, B).
+ * Filter (Sec. 3.1-3.2, Thm 2): U = R_{c,r,p*q}(B^{-1}A) Y, applied as
+ *   inner:  G(V) = sum_{i<=q} w_i K_i^{-1} B V,  K_i = p_i B - A   (Eq. linearsolve2)
+ *   outer:  U = sum_{j} c_j (s_j I - G)^{-1} G Y (+ (1/p) G Y, p odd) (Eq. linearsolve1abs)
+ * with the q inner factorisations done once (band LU, partial pivoting) and the
+ * p outer shifts solved together by multi-shift GMRES (one Krylov space per column).
+ *
+ * Conventions
+ *  - Complex numbers are ie_complex = {double re, im}, layout-identical to C99
+ *    double _Complex, CUDA double2 and numpy complex128.
+ *  - Blocks (Y, U, X, ...) are column-major n x k with leading dimension ld >= n.
+ *  - Pointers named d_* must be device pointers on the handle's device.
+ *    Pointers named *_any may be device or host memory (pageable or pinned);
+ *    host buffers are staged through the handle's device workspace on the
+ *    call's stream. Pointers named h_* must be host memory.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *  - Every function returns an ie_status; nothing is thrown across the ABI.
+ *    After IE_ERR_CUDA the handle should be destroyed.
+ *  - Calls on one handle must not overlap (the handle owns one workspace).
+ */
+#ifndef IE_H_
+#define IE_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct { double re, im; } ie_complex;
+
+typedef struct ie_handle_s* ie_handle;   /* opaque, owned by the library */
+
+typedef enum {
+  IE_OK = 0,
+  IE_ERR_ARG = 1,        /* invalid argument (sizes, NULL pointers, options) */
+  IE_ERR_CUDA = 2,       /* a CUDA runtime call or kernel failed */
+  IE_ERR_OOM = 3,        /* device allocation failed */
+  IE_ERR_SINGULAR = 4,   /* an LU pivot was exactly zero: a pole hit an eigenvalue (Prop. 1 case) */
+  IE_ERR_NOCONV = 5,     /* GMRES reached m_max or the driver reached max_outer; outputs still written */
+  IE_ERR_BREAKDOWN = 6,  /* reserved: orthogonalisation could not extend a basis */
+  IE_ERR_TIMEOUT = 7     /* a device-side bounded wait gave up (kernel returned early) */
+} ie_status;
+
+/* Sparse pencil in DIA form: M[i, i + offsets[d]] = dia[d * n + i] (entries with
+ * i + offsets[d] outside [0, n) are ignored). A and B share the offsets.
+ * Sec. 1 Eq. (problem). d_A_dia, d_B_dia: device, ndiag * n complex128, read
+ * during ie_create and copied (the caller may free them afterwards).
+ * h_offsets: host, ndiag entries, |offset| < n. ndiag <= 16. */
+typedef struct {
+  int64_t n;
+  int32_t ndiag;
+  const int64_t* h_offsets;
+  const ie_complex* d_A_dia;
+  const ie_complex* d_B_dia;
+} ie_pencil;
+
+/* Solver options (Alg. 1 / Alg. 2 REQUIRE lines; Sec. 6 preamble for defaults). */
+typedef struct {
+  int32_t k;              /* block width n_col (max columns per filter call), >= 1 */
+  int32_t driver;         /* 1 = Alg. 1 (fixed p, subspace iteration); 2 = Alg. 2 (p doubled) */
+  int32_t m_max;          /* max GMRES (Arnoldi) steps per column per filter application */
+  int32_t max_outer;      /* max outer iterations of the driver */
+  double tau_g;           /* ghost tolerance on e_i (Sec. 3.2), default 1e-2 */
+  double tau;             /* convergence tolerance on rho_i, default 1e-10 */
+  double gmres_tol;       /* per-shift relative GMRES residual, default 1e-12 */
+  int32_t sigma_is_center;/* 1: HSRR shift sigma = center (Sec. 6 preamble); 0: use sigma_re/im */
+  double sigma_re, sigma_im;
+  uint64_t seed;          /* seeds rank-guard replacement vectors and the random Y0 */
+} ie_opts;
+
+/* Fills defaults: k=16, driver=1, m_max=100, max_outer=10, tau_g=1e-2, tau=1e-10,
+ * gmres_tol=1e-12, sigma = center, seed = 0. */
+void ie_opts_default(ie_opts* opts);
+
+/* Counters and timings of the last ie_solve / ie_filter_apply on a handle. */
+typedef struct {
+  int32_t outer_iters;     /* outer iterations performed (ie_solve) */
+  int32_t n_found;         /* filtered pairs: in D and e_i < tau_g (Sec. 3.2) */
+  int32_t p_final;         /* outer order used by the last filter (Alg. 2 doubles it) */
+  int32_t gmres_iters_max; /* max Arnoldi steps over the columns, last filter */
+  int32_t gmres_iters_min;
+  int32_t converged;       /* 1 if the stop test was met */
+  int64_t g_columns;       /* columns G was applied to since create; solves = q * this */
+  double t_factor_ms;      /* ie_create: assembly + batched band LU */
+  double t_filter_ms;      /* total filter time of the last ie_solve (or the last filter call) */
+  double t_hsrr_ms;        /* total HSRR time of the last ie_solve */
+  double max_rho_found;    /* max rho_i over the filtered pairs */
+} ie_stats;
+
+/* ie_create: computes the inner poles/weights (Eq. pwtp, q points) and the outer
+ * shifts/weights (Thm 2, p roots of z^p = -1), assembles K_i = p_i B - A for all
+ * q poles into LAPACK band storage (kl = ku = max|offset|, ldab = 3*kl + 1) and
+ * factors all of them with partial pivoting in one cooperative launch
+ * (Alg. 1 lines 1-4). Requires p >= 1, q >= 1, radius > 0, 1 <= opts->k <= n.
+ * Returns IE_ERR_SINGULAR if a pivot is exactly zero (the handle is still
+ * created and must be destroyed). Synchronises the stream before returning. */
+ie_status ie_create(const ie_pencil* pencil, ie_complex center, double radius,
+                    int32_t p, int32_t q, const ie_opts* opts, void* stream,
+                    ie_handle* out);
+
+ie_status ie_destroy(ie_handle h);
+
+const char* ie_status_str(ie_status s);
+
+/* ie_filter_apply: U = R_{c,r,p*q}(B^{-1}A) Y by the composite rule (Alg. 1 lines
+ * 7-9): Ytilde = G(Y); per column multi-shift GMRES from x0 = 0 for all p outer
+ * shifts until every shift's relative residual <= gmres_tol (or m_max);
+ * U = sum_j c_j (s_j I - G)^{-1} Ytilde (+ (1/p) Ytilde for odd p).
+ * Y_any, U_any: n x k, k <= opts.k, ld >= n, device or host. Synchronises the
+ * stream (the GMRES loop tests convergence on the host after each step).
+ * Returns IE_ERR_NOCONV if a column reached m_max (U is still written). */
+ie_status ie_filter_apply(ie_handle h, const ie_complex* Y_any, int64_t ldy, int32_t k,
+                          ie_complex* U_any, int64_t ldu, void* stream);
+
+/* ie_apply_G: the inner operator alone, GV = G(V) = sum_i w_i K_i^{-1} B V
+ * (Eq. linearsolve2; Alg. 1 line 5). V_any, GV_any: n x k (k <= opts.k). */
+ie_status ie_apply_G(ie_handle h, const ie_complex* V_any, int64_t ldv, int32_t k,
+                     ie_complex* GV_any, int64_t ldgv, void* stream);
+
+/* ie_hsrr: the harmonic Rayleigh-Ritz step HSRR(A, B, U, sigma) (Sec. 2.1,
+ * Alg. SIsketch lines 4-7): V = orth(U) (CGS2 with rank guard), W = orth(AV - sigma BV),
+ * QZ of (W^*AV, W^*BV), lambda_i = (H_A)_ii/(H_B)_ii, x_i = V P_R V_R(:,i) scaled
+ * to unit norm; e_i (Eq. rel-error) and rho_i = ||Ax - lambda Bx|| /
+ * ((||A||_1 + |lambda| ||B||_1) ||x||). Outputs in QZ order (no sorting):
+ * h_lambda, h_e, h_rho host arrays of k entries (infinite Ritz values are
+ * returned as +inf); X_any n x k. Synchronises the stream. */
+ie_status ie_hsrr(ie_handle h, const ie_complex* U_any, int64_t ldu, int32_t k,
+                  ie_complex* h_lambda, ie_complex* X_any, int64_t ldx,
+                  double* h_e, double* h_rho, void* stream);
+
+/* ie_solve: all eigenpairs in D by Alg. 1 (opts.driver = 1) or Alg. 2 (= 2).
+ * Y0_any: n x opts.k starting block (orthonormal), or NULL for a seeded random
+ * orthonormal block. Outputs, ordered filtered pairs first (each group by
+ * |lambda - center| ascending): h_lambda (k, host), X_any (n x k, ldx),
+ * h_rho (k, host, nullable), h_e (k, host, nullable); *n_found = number of
+ * filtered pairs (Ritz value in D and e_i < tau_g). stats nullable.
+ * Returns IE_ERR_NOCONV if max_outer was reached without meeting the stop test. */
+ie_status ie_solve(ie_handle h, const ie_complex* Y0_any, int64_t ldy0,
+                   ie_complex* h_lambda, ie_complex* X_any, int64_t ldx,
+                   double* h_rho, double* h_e, int32_t* n_found, ie_stats* stats,
+                   void* stream);
+
+/* ie_spmv: Y = M X with M = A (which = 0) or B (which = 1), n x k blocks
+ * (the sparse products of Eq. linearsolve2 and of HSRR). */
+ie_status ie_spmv(ie_handle h, int32_t which, const ie_complex* X_any, int64_t ldx, int32_t k,
+                  ie_complex* Y_any, int64_t ldy, void* stream);
+
+/* ie_get_coeffs: copies the coefficients to host arrays (any may be NULL):
+ * h_poles, h_weights: q inner poles p_i and weights w_i (Eq. pwtp);
+ * h_shifts, h_cweights: the n_shift outer shifts s_j and weights c_j (Thm 2;
+ * for odd p the sigma = -1 root is left out, n_shift = p - p%2); *odd_coef = 1/p
+ * for odd p else 0. Arrays must hold q and p entries. */
+ie_status ie_get_coeffs(ie_handle h, ie_complex* h_poles, ie_complex* h_weights,
+                        ie_complex* h_shifts, ie_complex* h_cweights, int32_t* n_shift,
+                        double* odd_coef);
+
+/* ie_get_factor: copies pole i's band LU (LAPACK zgbtrf layout: column j holds
+ * rows j-kv..j+kl at offsets 0..ldab-1 with kv = 2*kl, ldab = 3*kl + 1; U in rows
+ * 0..kv, the multipliers of L below) and its 1-based pivot vector (LAPACK ipiv
+ * convention) into host arrays h_ab (ldab * n) and h_ipiv (n). *kl, *ldab set. */
+ie_status ie_get_factor(ie_handle h, int32_t pole, ie_complex* h_ab, int32_t* h_ipiv,
+                        int32_t* kl, int32_t* ldab);
+
+/* ie_get_stats: counters of the last call (see ie_stats). */
+ie_status ie_get_stats(ie_handle h, ie_stats* out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* IE_H_ */

@@ -1,0 +1,809 @@
+// C ABI of the interior eigensolver (include/ie.h): handle life cycle, the composite-rule
+// coefficients (Eq. pwtp; Thm 2), the filter (Alg. 1 lines 7-9), HSRR (Alg. SIsketch lines
+// 4-7) and the two drivers (Alg. 1, Alg. 2). Host code orchestrates kernels on one stream;
+// the GMRES loop reads k residuals back per Arnoldi step for its convergence test.
+#include <algorithm>
+#include <cmath>
+#include <complex>
+#include <cstring>
+#include <limits>
+#include <numeric>
+#include <vector>
+
+#include "ie_internal.cuh"
+
+typedef std::complex<double> zc;
+
+namespace {
+inline cplx to_c(zc z) { return make_double2(z.real(), z.imag()); }
+inline zc to_z(cplx c) { return zc(c.x, c.y); }
+inline zc to_z(ie_complex c) { return zc(c.re, c.im); }
+
+bool is_device_ptr(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+ie_status map_err(cudaError_t e) {
+  if (e == cudaSuccess) return IE_OK;
+  return e == cudaErrorMemoryAllocation ? IE_ERR_OOM : IE_ERR_CUDA;
+}
+}  // namespace
+
+#define CK(x)                                       \
+  do {                                              \
+    cudaError_t e_ = (x);                           \
+    if (e_ != cudaSuccess) return map_err(e_);      \
+  } while (0)
+#define CKS(x)                     \
+  do {                             \
+    ie_status s_ = (x);            \
+    if (s_ != IE_OK) return s_;    \
+  } while (0)
+
+struct ie_handle_s {
+  int dev = 0;
+  int64_t n = 0, n_pad = 0;
+  int kl = 0, kv = 0, ldab = 0, ndiag = 0;
+  int64_t offsets[IE_MAX_DIAG] = {};
+  DiaDev P{};
+  cplx* d_A = nullptr;
+  cplx* d_B = nullptr;
+  zc center;
+  double radius = 0;
+  int p = 0, q = 0;
+  ie_opts opts{};
+  zc sigma;
+  double normA = 0, normB = 0;
+  std::vector<zc> poles, weights;
+  cplx* d_poles = nullptr;
+  cplx* d_weights = nullptr;
+  // factors
+  cplx* AB = nullptr;
+  int* piv = nullptr;
+  cplx* dinv = nullptr;
+  unsigned* bar = nullptr;
+  int* status = nullptr;
+  int lu_ctas = 0;
+  // workspaces
+  int kmax = 0, m_max = 0;
+  cplx* Xp = nullptr;     // q * n * kmax
+  cplx* BVw = nullptr;    // n * kmax
+  cplx* Wb = nullptr;     // n * kmax
+  cplx* Yb = nullptr;     // n * kmax  (current block / host staging)
+  cplx* Ub = nullptr;     // n * kmax
+  cplx* Vh = nullptr;     // HSRR V
+  cplx* AVh = nullptr;
+  cplx* BVh = nullptr;
+  cplx* Wh = nullptr;
+  cplx* Xh = nullptr;
+  cplx* Ah = nullptr;     // k*k
+  cplx* Bh = nullptr;
+  cplx* Zq = nullptr;     // 2*k*k
+  cplx* Mq = nullptr;     // k*k
+  cplx* alpha = nullptr;  // k
+  cplx* betaq = nullptr;
+  cplx* d_lam = nullptr;
+  int* d_perm = nullptr;
+  int* d_flags = nullptr;
+  double* d_rn = nullptr;  // 3*k
+  // Krylov
+  KrylovDev K{};
+  int* d_act = nullptr;
+  int64_t* d_off = nullptr;
+  double* d_res = nullptr;
+  cplx* hbuf = nullptr;
+  double* scratch = nullptr;
+  // Givens / combine (sized for nshift_cap shifts)
+  int nshift_cap = 0;
+  cplx* rot_c = nullptr;
+  cplx* rot_s = nullptr;
+  cplx* gvec = nullptr;
+  cplx* Rscr = nullptr;
+  cplx* zbuf = nullptr;
+  cplx* d_shifts = nullptr;
+  cplx* d_cw = nullptr;
+  // host mirrors
+  std::vector<int> jc_h;
+  std::vector<double> beta_h;
+  std::vector<char> conv_h;
+  ie_stats stats{};
+  int64_t g_columns = 0;
+  uint32_t salt = 1;
+  std::vector<void*> allocs;
+
+  template <typename T>
+  cudaError_t alloc(T** p_, size_t count) {
+    void* v = nullptr;
+    cudaError_t e = cudaMalloc(&v, std::max<size_t>(count, 1) * sizeof(T));
+    if (e != cudaSuccess) return e;
+    allocs.push_back(v);
+    *p_ = (T*)v;
+    return cudaSuccess;
+  }
+  void release(void* p_) {
+    if (!p_) return;
+    auto it = std::find(allocs.begin(), allocs.end(), p_);
+    if (it != allocs.end()) allocs.erase(it);
+    cudaFree(p_);
+  }
+  ~ie_handle_s() {
+    for (void* v : allocs) cudaFree(v);
+  }
+};
+
+extern "C" void ie_opts_default(ie_opts* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->k = 16;
+  o->driver = 1;
+  o->m_max = 100;
+  o->max_outer = 10;
+  o->tau_g = 1e-2;
+  o->tau = 1e-10;
+  o->gmres_tol = 1e-12;
+  o->sigma_is_center = 1;
+  o->seed = 0;
+}
+
+extern "C" const char* ie_status_str(ie_status s) {
+  switch (s) {
+    case IE_OK: return "IE_OK";
+    case IE_ERR_ARG: return "IE_ERR_ARG: invalid argument";
+    case IE_ERR_CUDA: return "IE_ERR_CUDA: CUDA error";
+    case IE_ERR_OOM: return "IE_ERR_OOM: device allocation failed";
+    case IE_ERR_SINGULAR: return "IE_ERR_SINGULAR: zero pivot in the band LU";
+    case IE_ERR_NOCONV: return "IE_ERR_NOCONV: iteration limit reached";
+    case IE_ERR_BREAKDOWN: return "IE_ERR_BREAKDOWN: orthogonalisation breakdown";
+    case IE_ERR_TIMEOUT: return "IE_ERR_TIMEOUT: a device-side bounded wait gave up";
+  }
+  return "unknown ie_status";
+}
+
+// ------------------------------ coefficients --------------------------------------------------
+// Eq. (pwtp): p_i = c + r e^{i theta_i}, w_i = r e^{i theta_i} / q, theta_i = (2i-1) pi / q.
+static void inner_coeffs(zc c, double r, int q, std::vector<zc>& poles, std::vector<zc>& w) {
+  poles.resize(q);
+  w.resize(q);
+  for (int i = 1; i <= q; ++i) {
+    const double th = (2.0 * i - 1.0) * M_PI / q;
+    const zc e(std::cos(th), std::sin(th));
+    poles[i - 1] = c + r * e;
+    w[i - 1] = r * e / (double)q;
+  }
+}
+// Thm 2: sigma_j = e^{i (2j-1) pi / p}; s_j = 1/(1+sigma_j); c_j = -(1/p) sigma_j/(1+sigma_j);
+// for odd p the root sigma = -1 (j = (p+1)/2) is left out and contributes (1/p) R_q.
+static void outer_coeffs(int p, std::vector<zc>& s, std::vector<zc>& cw, double& odd) {
+  s.clear();
+  cw.clear();
+  odd = (p % 2) ? 1.0 / p : 0.0;
+  for (int j = 1; j <= p; ++j) {
+    if ((p % 2) && j == (p + 1) / 2) continue;
+    const double th = (2.0 * j - 1.0) * M_PI / p;
+    const zc sg(std::cos(th), std::sin(th));
+    s.push_back(1.0 / (1.0 + sg));
+    cw.push_back(-(1.0 / p) * sg / (1.0 + sg));
+  }
+}
+
+// ------------------------------ workspace -------------------------------------------------------
+static ie_status ensure_shift_capacity(ie_handle h, int nshift) {
+  if (nshift <= h->nshift_cap) return IE_OK;
+  int cap = std::max(nshift, 2 * h->nshift_cap);
+  const int64_t k = h->kmax, M = h->m_max;
+  for (void* p_ : {(void*)h->rot_c, (void*)h->rot_s, (void*)h->gvec, (void*)h->Rscr,
+                   (void*)h->zbuf, (void*)h->d_shifts, (void*)h->d_cw})
+    h->release(p_);
+  CK(h->alloc(&h->rot_c, (size_t)(k * cap * M)));
+  CK(h->alloc(&h->rot_s, (size_t)(k * cap * M)));
+  CK(h->alloc(&h->gvec, (size_t)(k * cap * (M + 1))));
+  CK(h->alloc(&h->Rscr, (size_t)(k * cap * M * M)));
+  CK(h->alloc(&h->zbuf, (size_t)(2 * k * cap * M + k * cap * (M + 1) + k * (M + 1))));
+  CK(h->alloc(&h->d_shifts, (size_t)cap));
+  CK(h->alloc(&h->d_cw, (size_t)cap));
+  h->nshift_cap = cap;
+  return IE_OK;
+}
+
+static ie_status alloc_workspace(ie_handle h) {
+  const int64_t n = h->n, k = h->kmax, M = h->m_max, q = h->q;
+  CK(h->alloc(&h->Xp, (size_t)(q * n * k)));
+  CK(h->alloc(&h->BVw, (size_t)(n * k)));
+  CK(h->alloc(&h->Wb, (size_t)(n * k)));
+  CK(h->alloc(&h->Yb, (size_t)(n * k)));
+  CK(h->alloc(&h->Ub, (size_t)(n * k)));
+  CK(h->alloc(&h->Vh, (size_t)(n * k)));
+  CK(h->alloc(&h->AVh, (size_t)(n * k)));
+  CK(h->alloc(&h->BVh, (size_t)(n * k)));
+  CK(h->alloc(&h->Wh, (size_t)(n * k)));
+  CK(h->alloc(&h->Xh, (size_t)(n * k)));
+  CK(h->alloc(&h->Ah, (size_t)(k * k)));
+  CK(h->alloc(&h->Bh, (size_t)(k * k)));
+  CK(h->alloc(&h->Zq, (size_t)(2 * k * k)));
+  CK(h->alloc(&h->Mq, (size_t)(k * k)));
+  CK(h->alloc(&h->alpha, (size_t)k));
+  CK(h->alloc(&h->betaq, (size_t)k));
+  CK(h->alloc(&h->d_lam, (size_t)k));
+  CK(h->alloc(&h->d_perm, (size_t)k));
+  CK(h->alloc(&h->d_flags, (size_t)k));
+  CK(h->alloc(&h->d_rn, (size_t)(3 * k)));
+  // Krylov bases
+  CK(h->alloc(&h->K.V, (size_t)(k * (M + 1) * n)));
+  CK(h->alloc(&h->K.H, (size_t)(k * (M + 1) * M)));
+  CK(h->alloc(&h->K.beta, (size_t)k));
+  CK(h->alloc(&h->K.jc, (size_t)k));
+  CK(h->alloc(&h->K.brk, (size_t)k));
+  h->K.n = n;
+  h->K.m_max = (int)M;
+  CK(cudaMemset(h->K.H, 0, sizeof(cplx) * (size_t)(k * (M + 1) * M)));
+  CK(h->alloc(&h->d_act, (size_t)k));
+  CK(h->alloc(&h->d_off, (size_t)k));
+  CK(h->alloc(&h->d_res, (size_t)k));
+  const int64_t LD = M + 2;
+  CK(h->alloc(&h->hbuf, (size_t)(2 * k * LD + k + 3 * (k + 1) + 16)));
+  const int64_t nch512 = (n + 511) / 512, nblk = (n + 255) / 256;
+  int64_t need = 2 * k * nch512 * LD + k * nblk;                 // Arnoldi partials
+  need = std::max<int64_t>(need, 2 * nch512 * k * k);            // Gram partials
+  need = std::max<int64_t>(need, 3 * k * nblk);                  // residual partials
+  need = std::max<int64_t>(need, 2 * nch512 * (k + 1));          // orth partials
+  need = std::max<int64_t>(need, 2 * (k * 64 + k));              // column norms
+  CK(h->alloc(&h->scratch, (size_t)(need + 1024)));
+  CKS(ensure_shift_capacity(h, std::max(1, h->p)));
+  h->jc_h.assign(k, 0);
+  h->beta_h.assign(k, 0.0);
+  h->conv_h.assign(k, 0);
+  return IE_OK;
+}
+
+// ------------------------------ create / destroy -------------------------------------------------
+extern "C" ie_status ie_create(const ie_pencil* pen, ie_complex center, double radius, int32_t p,
+                               int32_t q, const ie_opts* opts_in, void* stream, ie_handle* out) {
+  if (!pen || !out || !pen->h_offsets || !pen->d_A_dia || !pen->d_B_dia) return IE_ERR_ARG;
+  *out = nullptr;
+  ie_opts opts;
+  if (opts_in) opts = *opts_in; else ie_opts_default(&opts);
+  if (pen->n < 2 || pen->ndiag < 1 || pen->ndiag > IE_MAX_DIAG) return IE_ERR_ARG;
+  if (p < 1 || q < 1 || !(radius > 0.0) || !std::isfinite(radius)) return IE_ERR_ARG;
+  if (opts.k < 1 || opts.k > pen->n || opts.m_max < 1 || opts.m_max > 1000 ||
+      opts.max_outer < 1 || (opts.driver != 1 && opts.driver != 2))
+    return IE_ERR_ARG;
+  if (!(opts.gmres_tol > 0) || !(opts.tau > 0) || !(opts.tau_g > 0)) return IE_ERR_ARG;
+  int kl = 0;
+  for (int d = 0; d < pen->ndiag; ++d) {
+    const int64_t o = pen->h_offsets[d];
+    if (o <= -pen->n || o >= pen->n) return IE_ERR_ARG;
+    kl = (int)std::max<int64_t>(kl, o < 0 ? -o : o);
+  }
+  if (kl < 1 || 2 * kl + 1 > 1280) return IE_ERR_ARG;   // band solve supports half bandwidth <= 639
+  cudaStream_t s = (cudaStream_t)stream;
+  ie_handle h = new ie_handle_s();
+  cudaGetDevice(&h->dev);
+  h->n = pen->n;
+  h->n_pad = (pen->n + 3) / 4 * 4;
+  h->kl = kl;
+  h->kv = 2 * kl;
+  h->ldab = 3 * kl + 1;
+  h->ndiag = pen->ndiag;
+  h->center = to_z(center);
+  h->radius = radius;
+  h->p = p;
+  h->q = q;
+  h->opts = opts;
+  h->kmax = opts.k;
+  h->m_max = opts.m_max;
+  h->sigma = opts.sigma_is_center ? h->center : zc(opts.sigma_re, opts.sigma_im);
+  auto fail = [&](ie_status st) { delete h; return st; };
+  const size_t dia_bytes = sizeof(cplx) * (size_t)pen->ndiag * (size_t)pen->n;
+  if (h->alloc(&h->d_A, (size_t)pen->ndiag * pen->n) != cudaSuccess) return fail(IE_ERR_OOM);
+  if (h->alloc(&h->d_B, (size_t)pen->ndiag * pen->n) != cudaSuccess) return fail(IE_ERR_OOM);
+  if (cudaMemcpyAsync(h->d_A, pen->d_A_dia, dia_bytes, cudaMemcpyDefault, s) != cudaSuccess ||
+      cudaMemcpyAsync(h->d_B, pen->d_B_dia, dia_bytes, cudaMemcpyDefault, s) != cudaSuccess)
+    return fail(IE_ERR_CUDA);
+  h->P.n = h->n;
+  h->P.ndiag = h->ndiag;
+  for (int d = 0; d < h->ndiag; ++d) h->P.off[d] = h->offsets[d] = pen->h_offsets[d];
+  h->P.A = h->d_A;
+  h->P.B = h->d_B;
+  // coefficients
+  inner_coeffs(h->center, radius, q, h->poles, h->weights);
+  std::vector<cplx> tmp(q);
+  if (h->alloc(&h->d_poles, q) != cudaSuccess || h->alloc(&h->d_weights, q) != cudaSuccess)
+    return fail(IE_ERR_OOM);
+  for (int i = 0; i < q; ++i) tmp[i] = to_c(h->poles[i]);
+  cudaMemcpyAsync(h->d_poles, tmp.data(), sizeof(cplx) * q, cudaMemcpyHostToDevice, s);
+  cudaStreamSynchronize(s);
+  for (int i = 0; i < q; ++i) tmp[i] = to_c(h->weights[i]);
+  cudaMemcpyAsync(h->d_weights, tmp.data(), sizeof(cplx) * q, cudaMemcpyHostToDevice, s);
+  cudaStreamSynchronize(s);
+  // norms ||A||_1, ||B||_1
+  double* dn = nullptr;
+  if (h->alloc(&dn, 2) != cudaSuccess) return fail(IE_ERR_OOM);
+  launch_norm1_cols(h->P, 0, dn, nullptr, s);
+  launch_norm1_cols(h->P, 1, dn + 1, nullptr, s);
+  double hn[2];
+  if (cudaMemcpyAsync(hn, dn, sizeof(hn), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    return fail(IE_ERR_CUDA);
+  h->normA = hn[0];
+  h->normB = hn[1];
+  // factors
+  if (h->alloc(&h->AB, (size_t)q * h->n_pad * h->ldab) != cudaSuccess ||
+      h->alloc(&h->piv, (size_t)q * h->n_pad) != cudaSuccess ||
+      h->alloc(&h->dinv, (size_t)q * h->n_pad) != cudaSuccess ||
+      h->alloc(&h->bar, (size_t)2 * q) != cudaSuccess ||
+      h->alloc(&h->status, ST_COUNT) != cudaSuccess)
+    return fail(IE_ERR_OOM);
+  cudaMemsetAsync(h->status, 0, sizeof(int) * ST_COUNT, s);
+  cudaMemsetAsync(h->piv, 0, sizeof(int) * (size_t)q * h->n_pad, s);
+  cudaMemsetAsync(h->dinv, 0, sizeof(cplx) * (size_t)q * h->n_pad, s);
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  cudaEventRecord(e0, s);
+  launch_assemble(h->P, h->d_poles, q, kl, h->ldab, h->n_pad, h->AB, s);
+  cudaError_t le = launch_band_lu(q, h->n, kl, h->ldab, h->n_pad, h->AB, h->piv, h->dinv, h->bar,
+                                  h->status, s, &h->lu_ctas);
+  cudaEventRecord(e1, s);
+  if (le != cudaSuccess) { cudaEventDestroy(e0); cudaEventDestroy(e1); return fail(map_err(le)); }
+  if (cudaStreamSynchronize(s) != cudaSuccess) {
+    cudaEventDestroy(e0); cudaEventDestroy(e1);
+    return fail(IE_ERR_CUDA);
+  }
+  float ms = 0;
+  cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  h->stats.t_factor_ms = ms;
+  int st[ST_COUNT];
+  cudaMemcpy(st, h->status, sizeof(st), cudaMemcpyDeviceToHost);
+  if (st[ST_TIMEOUT]) return fail(IE_ERR_TIMEOUT);
+  ie_status ws = alloc_workspace(h);
+  if (ws != IE_OK) return fail(ws);
+  if (cudaGetLastError() != cudaSuccess) return fail(IE_ERR_CUDA);
+  *out = h;
+  return st[ST_SINGULAR] ? IE_ERR_SINGULAR : IE_OK;
+}
+
+extern "C" ie_status ie_destroy(ie_handle h) {
+  if (!h) return IE_ERR_ARG;
+  delete h;
+  return IE_OK;
+}
+
+// ------------------------------ host/device staging ----------------------------------------------
+static ie_status stage_in(ie_handle h, const ie_complex* src, int64_t ld, int k, cplx* dst,
+                          cudaStream_t s, const cplx** out) {
+  if (is_device_ptr(src)) {
+    *out = (const cplx*)src;
+    return IE_OK;
+  }
+  CK(cudaMemcpy2DAsync(dst, sizeof(cplx) * h->n, src, sizeof(cplx) * ld, sizeof(cplx) * h->n, k,
+                       cudaMemcpyHostToDevice, s));
+  *out = dst;
+  return IE_OK;
+}
+static ie_status stage_out(ie_handle h, const cplx* src, int64_t lds, int k, ie_complex* dst,
+                           int64_t ldd, cudaStream_t s) {
+  if ((const void*)src == (const void*)dst) return IE_OK;
+  CK(cudaMemcpy2DAsync(dst, sizeof(cplx) * ldd, src, sizeof(cplx) * lds, sizeof(cplx) * h->n, k,
+                       cudaMemcpyDefault, s));
+  return IE_OK;
+}
+static ie_status check_status(ie_handle h, cudaStream_t s) {
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(s));
+  int st[ST_COUNT];
+  CK(cudaMemcpy(st, h->status, sizeof(st), cudaMemcpyDeviceToHost));
+  if (st[ST_TIMEOUT]) return IE_ERR_TIMEOUT;
+  return IE_OK;
+}
+
+// ------------------------------ inner operator G ----------------------------------------------
+// GV = sum_i w_i K_i^{-1} B V (Eq. linearsolve2). V columns at V + off[c] when d_off != null.
+static ie_status apply_G_dev(ie_handle h, const cplx* V, int64_t ldv, const int64_t* d_off, int k,
+                             cplx* GV, int64_t ldg, cudaStream_t s) {
+  if (k <= 0) return IE_OK;
+  launch_spmv(h->P, make_double2(0, 0), make_double2(1, 0), V, ldv, d_off, k, h->BVw, h->n, s);
+  CK(launch_band_solve(h->q, h->n, h->kl, h->ldab, h->n_pad, h->AB, h->piv, h->dinv, h->d_weights,
+                       h->BVw, h->n, k, h->Xp, h->n, h->n * (int64_t)h->kmax, h->status, s));
+  launch_pole_sum(h->q, h->n, k, h->Xp, h->n, h->n * (int64_t)h->kmax, GV, ldg, s);
+  h->g_columns += k;
+  return IE_OK;
+}
+
+// ------------------------------ filter (multi-shift GMRES) -----------------------------------
+// U = sum_j c_j (s_j I - G)^{-1} Ytilde (+ odd Ytilde). With reuse, the Krylov spaces of the
+// previous call are kept and only extended (Alg. 2 line 9).
+static ie_status filter_dev(ie_handle h, const cplx* Y, int64_t ldy, int k, cplx* U, int64_t ldu,
+                            int p_use, bool reuse, cudaStream_t s, bool* noconv) {
+  const int64_t n = h->n;
+  *noconv = false;
+  if (!reuse) {
+    CKS(apply_G_dev(h, Y, ldy, nullptr, k, h->Wb, n, s));      // Ytilde = G(Y)
+    launch_krylov_start(h->K, k, h->Wb, n, h->scratch, s);
+    CK(cudaMemcpyAsync(h->beta_h.data(), h->K.beta, sizeof(double) * k, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    for (int c = 0; c < k; ++c) h->jc_h[c] = 0;
+  }
+  std::vector<zc> sh, cw;
+  double odd = 0;
+  outer_coeffs(p_use, sh, cw, odd);
+  const int nshift = (int)sh.size();
+  CKS(ensure_shift_capacity(h, std::max(nshift, 1)));
+  {
+    std::vector<cplx> a(nshift), b(nshift);
+    for (int i = 0; i < nshift; ++i) { a[i] = to_c(sh[i]); b[i] = to_c(cw[i]); }
+    if (nshift) {
+      CK(cudaMemcpyAsync(h->d_shifts, a.data(), sizeof(cplx) * nshift, cudaMemcpyHostToDevice, s));
+      CK(cudaMemcpyAsync(h->d_cw, b.data(), sizeof(cplx) * nshift, cudaMemcpyHostToDevice, s));
+      CK(cudaStreamSynchronize(s));
+    }
+  }
+  const double tol = h->opts.gmres_tol;
+  std::vector<int> act;
+  std::vector<double> res(k);
+  // convergence state of every column for the current shift set
+  for (int c = 0; c < k; ++c) h->conv_h[c] = (h->beta_h[c] > 0.0) ? 0 : 1;
+  if (nshift == 0) {
+    for (int c = 0; c < k; ++c) h->conv_h[c] = 1;
+  } else if (reuse) {
+    act.clear();
+    for (int c = 0; c < k; ++c)
+      if (!h->conv_h[c] && h->jc_h[c] > 0) act.push_back(c);
+    if (!act.empty()) {
+      CK(cudaMemcpyAsync(h->d_act, act.data(), sizeof(int) * act.size(), cudaMemcpyHostToDevice, s));
+      launch_givens(h->K, h->d_act, (int)act.size(), h->d_shifts, nshift, h->rot_c, h->rot_s,
+                    h->gvec, 1, h->d_res, s);
+      CK(cudaMemcpyAsync(res.data(), h->d_res, sizeof(double) * act.size(), cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      for (size_t i = 0; i < act.size(); ++i)
+        if (res[i] <= tol) h->conv_h[act[i]] = 1;
+    }
+  }
+  while (true) {
+    act.clear();
+    for (int c = 0; c < k; ++c)
+      if (!h->conv_h[c]) {
+        if (h->jc_h[c] >= h->m_max) { *noconv = true; continue; }
+        act.push_back(c);
+      }
+    if (act.empty()) break;
+    const int kact = (int)act.size();
+    CK(cudaMemcpyAsync(h->d_act, act.data(), sizeof(int) * kact, cudaMemcpyHostToDevice, s));
+    launch_active_offsets(h->K, h->d_act, kact, h->d_off, s);
+    CKS(apply_G_dev(h, h->K.V, n, h->d_off, kact, h->Wb, n, s));   // w = G v_j
+    launch_arnoldi_cgs2(h->K, h->d_act, kact, h->Wb, n, h->hbuf, h->scratch, s);
+    launch_givens(h->K, h->d_act, kact, h->d_shifts, nshift, h->rot_c, h->rot_s, h->gvec, 0,
+                  h->d_res, s);
+    CK(cudaMemcpyAsync(res.data(), h->d_res, sizeof(double) * kact, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    for (int i = 0; i < kact; ++i) {
+      const int c = act[i];
+      h->jc_h[c] += 1;
+      if (res[i] <= tol) h->conv_h[c] = 1;
+    }
+  }
+  launch_krylov_combine(h->K, k, h->d_shifts, h->d_cw, nshift, odd, h->Rscr, h->zbuf, U, ldu, s);
+  int mx = 0, mn = 1 << 30;
+  for (int c = 0; c < k; ++c) { mx = std::max(mx, h->jc_h[c]); mn = std::min(mn, h->jc_h[c]); }
+  h->stats.gmres_iters_max = mx;
+  h->stats.gmres_iters_min = (k > 0) ? mn : 0;
+  h->stats.p_final = p_use;
+  return check_status(h, s);
+}
+
+extern "C" ie_status ie_filter_apply(ie_handle h, const ie_complex* Y_any, int64_t ldy, int32_t k,
+                                     ie_complex* U_any, int64_t ldu, void* stream) {
+  if (!h || !Y_any || !U_any || k < 1 || k > h->kmax || ldy < h->n || ldu < h->n) return IE_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  cudaEventRecord(e0, s);
+  const cplx* Y;
+  CKS(stage_in(h, Y_any, ldy, k, h->Yb, s, &Y));
+  const bool udev = is_device_ptr(U_any);
+  cplx* U = udev ? (cplx*)U_any : h->Ub;
+  const int64_t ldU = udev ? ldu : h->n;
+  bool nc = false;
+  ie_status st = filter_dev(h, Y, Y == h->Yb ? h->n : ldy, k, U, ldU, h->p, false, s, &nc);
+  if (st == IE_OK && !udev) st = stage_out(h, U, ldU, k, U_any, ldu, s);
+  cudaEventRecord(e1, s);
+  cudaStreamSynchronize(s);
+  float ms = 0;
+  cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  h->stats.t_filter_ms = ms;
+  h->stats.g_columns = h->g_columns;
+  if (st != IE_OK) return st;
+  return nc ? IE_ERR_NOCONV : IE_OK;
+}
+
+extern "C" ie_status ie_apply_G(ie_handle h, const ie_complex* V_any, int64_t ldv, int32_t k,
+                                ie_complex* GV_any, int64_t ldgv, void* stream) {
+  if (!h || !V_any || !GV_any || k < 1 || k > h->kmax || ldv < h->n || ldgv < h->n) return IE_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  const cplx* V;
+  CKS(stage_in(h, V_any, ldv, k, h->Yb, s, &V));
+  const bool gdev = is_device_ptr(GV_any);
+  cplx* G = gdev ? (cplx*)GV_any : h->Ub;
+  const int64_t ldG = gdev ? ldgv : h->n;
+  CKS(apply_G_dev(h, V, V == h->Yb ? h->n : ldv, nullptr, k, G, ldG, s));
+  if (!gdev) CKS(stage_out(h, G, ldG, k, GV_any, ldgv, s));
+  h->stats.g_columns = h->g_columns;
+  return check_status(h, s);
+}
+
+extern "C" ie_status ie_spmv(ie_handle h, int32_t which, const ie_complex* X_any, int64_t ldx,
+                             int32_t k, ie_complex* Y_any, int64_t ldy, void* stream) {
+  if (!h || !X_any || !Y_any || k < 1 || k > h->kmax || ldx < h->n || ldy < h->n ||
+      (which != 0 && which != 1))
+    return IE_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  const cplx* X;
+  CKS(stage_in(h, X_any, ldx, k, h->Yb, s, &X));
+  const bool ydev = is_device_ptr(Y_any);
+  cplx* Y = ydev ? (cplx*)Y_any : h->Ub;
+  const int64_t ldY = ydev ? ldy : h->n;
+  const cplx one = make_double2(1, 0), zero = make_double2(0, 0);
+  launch_spmv(h->P, which == 0 ? one : zero, which == 1 ? one : zero, X, X == h->Yb ? h->n : ldx,
+              nullptr, k, Y, ldY, s);
+  if (!ydev) CKS(stage_out(h, Y, ldY, k, Y_any, ldy, s));
+  return check_status(h, s);
+}
+
+// ------------------------------ HSRR ------------------------------------------------------------
+// Results: h->Xh (n x k Ritz vectors, unit norm), lam/e/rho on the host (QZ order).
+static ie_status hsrr_dev(ie_handle h, const cplx* U, int64_t ldu, int k, cudaStream_t s,
+                          std::vector<zc>& lam, std::vector<double>& e, std::vector<double>& rho) {
+  const int64_t n = h->n;
+  const uint64_t seed = h->opts.seed;
+  launch_copy_cols(n, k, U, ldu, h->Vh, n, s);
+  launch_orth_cgs2(n, k, h->Vh, n, seed, h->salt++, h->hbuf, h->scratch, h->d_flags, s);  // V
+  const cplx one = make_double2(1, 0), zero = make_double2(0, 0);
+  launch_spmv(h->P, one, zero, h->Vh, n, nullptr, k, h->AVh, n, s);                       // AV
+  launch_spmv(h->P, zero, one, h->Vh, n, nullptr, k, h->BVh, n, s);                       // BV
+  launch_spmv(h->P, one, to_c(-h->sigma), h->Vh, n, nullptr, k, h->Wh, n, s);            // AV - sigma BV
+  launch_orth_cgs2(n, k, h->Wh, n, seed, h->salt++, h->hbuf, h->scratch, h->d_flags, s);  // W
+  launch_gram(n, k, h->Wh, n, h->AVh, n, h->Ah, (cplx*)h->scratch, s);                    // W^H A V
+  launch_gram(n, k, h->Wh, n, h->BVh, n, h->Bh, (cplx*)h->scratch, s);                    // W^H B V
+  CK(launch_qz(k, h->Ah, h->Bh, h->Zq, h->alpha, h->betaq, h->Mq, h->status, s));
+  std::vector<cplx> al(k), be(k);
+  CK(cudaMemcpyAsync(al.data(), h->alpha, sizeof(cplx) * k, cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(be.data(), h->betaq, sizeof(cplx) * k, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  lam.resize(k);
+  std::vector<cplx> lamc(k);
+  const double inf = std::numeric_limits<double>::infinity();
+  for (int i = 0; i < k; ++i) {
+    const zc b = to_z(be[i]);
+    lam[i] = (b == zc(0, 0)) ? zc(inf, 0) : to_z(al[i]) / b;
+    lamc[i] = std::isfinite(lam[i].real()) && std::isfinite(lam[i].imag()) ? to_c(lam[i])
+                                                                            : make_double2(inf, 0);
+  }
+  CK(cudaMemcpyAsync(h->d_lam, lamc.data(), sizeof(cplx) * k, cudaMemcpyHostToDevice, s));
+  launch_gemm_small(n, k, h->Vh, n, h->Mq, h->Xh, n, s);                                  // x = V P_R V_R
+  launch_normalize_cols(n, k, h->Xh, n, h->scratch, s);
+  launch_residual_norms(h->P, k, h->Xh, n, h->d_lam, h->d_rn, h->scratch, s);
+  std::vector<double> rn(3 * k);
+  CK(cudaMemcpyAsync(rn.data(), h->d_rn, sizeof(double) * 3 * k, cudaMemcpyDeviceToHost, s));
+  CKS(check_status(h, s));
+  e.resize(k);
+  rho.resize(k);
+  const double scale_e = std::abs(h->center) + h->radius;
+  for (int i = 0; i < k; ++i) {
+    const bool fin = std::isfinite(lam[i].real()) && std::isfinite(lam[i].imag());
+    const double r = std::sqrt(rn[3 * i]), bx = std::sqrt(rn[3 * i + 1]), xn = std::sqrt(rn[3 * i + 2]);
+    e[i] = fin ? r / (scale_e * bx) : inf;
+    rho[i] = fin ? r / ((h->normA + std::abs(lam[i]) * h->normB) * xn) : inf;
+  }
+  return IE_OK;
+}
+
+extern "C" ie_status ie_hsrr(ie_handle h, const ie_complex* U_any, int64_t ldu, int32_t k,
+                             ie_complex* h_lambda, ie_complex* X_any, int64_t ldx, double* h_e,
+                             double* h_rho, void* stream) {
+  if (!h || !U_any || k < 1 || k > h->kmax || ldu < h->n || (X_any && ldx < h->n)) return IE_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  const cplx* U;
+  CKS(stage_in(h, U_any, ldu, k, h->Ub, s, &U));
+  std::vector<zc> lam;
+  std::vector<double> e, rho;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  cudaEventRecord(e0, s);
+  ie_status st = hsrr_dev(h, U, U == h->Ub ? h->n : ldu, k, s, lam, e, rho);
+  cudaEventRecord(e1, s);
+  cudaStreamSynchronize(s);
+  float ms = 0;
+  cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  h->stats.t_hsrr_ms = ms;
+  if (st != IE_OK) return st;
+  for (int i = 0; i < k; ++i) {
+    if (h_lambda) { h_lambda[i].re = lam[i].real(); h_lambda[i].im = lam[i].imag(); }
+    if (h_e) h_e[i] = e[i];
+    if (h_rho) h_rho[i] = rho[i];
+  }
+  if (X_any) CKS(stage_out(h, h->Xh, h->n, k, X_any, ldx, s));
+  return check_status(h, s);
+}
+
+// ------------------------------ drivers ----------------------------------------------------------
+static bool in_disk(ie_handle h, zc l) {
+  return std::isfinite(l.real()) && std::isfinite(l.imag()) && std::abs(l - h->center) < h->radius;
+}
+
+extern "C" ie_status ie_solve(ie_handle h, const ie_complex* Y0_any, int64_t ldy0,
+                              ie_complex* h_lambda, ie_complex* X_any, int64_t ldx, double* h_rho,
+                              double* h_e, int32_t* n_found, ie_stats* stats, void* stream) {
+  if (!h || !h_lambda || !X_any || !n_found || ldx < h->n) return IE_ERR_ARG;
+  if (Y0_any && ldy0 < h->n) return IE_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int k = h->kmax;
+  const int64_t n = h->n;
+  // starting block
+  if (Y0_any) {
+    if (is_device_ptr(Y0_any)) {
+      launch_copy_cols(n, k, (const cplx*)Y0_any, ldy0, h->Yb, n, s);
+    } else {
+      CK(cudaMemcpy2DAsync(h->Yb, sizeof(cplx) * n, Y0_any, sizeof(cplx) * ldy0, sizeof(cplx) * n,
+                           k, cudaMemcpyHostToDevice, s));
+    }
+  } else {
+    launch_random_block(n, k, h->Yb, n, h->opts.seed, 0xA5A5u, s);
+    launch_orth_cgs2(n, k, h->Yb, n, h->opts.seed, 0x5A5Au, h->hbuf, h->scratch, h->d_flags, s);
+  }
+  h->salt = 1;
+  ie_stats& S = h->stats;
+  const double t_factor = S.t_factor_ms;
+  S = ie_stats{};
+  S.t_factor_ms = t_factor;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  std::vector<zc> lam;
+  std::vector<double> e, rho;
+  std::vector<char> filt;
+  int prev = -1, nf = 0;
+  bool converged = false, any_noconv = false;
+  int pc = h->p;
+  ie_status st = IE_OK;
+  for (int t = 1; t <= h->opts.max_outer; ++t) {
+    cudaEventRecord(e0, s);
+    bool nc = false;
+    if (h->opts.driver == 1) {
+      st = filter_dev(h, h->Yb, n, k, h->Ub, n, h->p, false, s, &nc);       // Alg. 1 lines 8-10
+    } else {
+      st = filter_dev(h, h->Yb, n, k, h->Ub, n, pc, t > 1, s, &nc);         // Alg. 2 lines 9-10
+    }
+    cudaEventRecord(e1, s);
+    if (st != IE_OK) break;
+    cudaStreamSynchronize(s);
+    float ms = 0;
+    cudaEventElapsedTime(&ms, e0, e1);
+    S.t_filter_ms += ms;
+    any_noconv |= nc;
+    cudaEventRecord(e0, s);
+    st = hsrr_dev(h, h->Ub, n, k, s, lam, e, rho);                           // line 11
+    cudaEventRecord(e1, s);
+    if (st != IE_OK) break;
+    cudaStreamSynchronize(s);
+    cudaEventElapsedTime(&ms, e0, e1);
+    S.t_hsrr_ms += ms;
+    // ghost filter and stop test (line 12; Sec. 3.2)
+    filt.assign(k, 0);
+    nf = 0;
+    bool all_conv = true;
+    double mr = 0.0;
+    for (int i = 0; i < k; ++i) {
+      filt[i] = in_disk(h, lam[i]) && e[i] < h->opts.tau_g;
+      if (filt[i]) {
+        ++nf;
+        mr = std::max(mr, rho[i]);
+        if (!(rho[i] < h->opts.tau)) all_conv = false;
+      }
+    }
+    S.outer_iters = t;
+    S.n_found = nf;
+    S.max_rho_found = mr;
+    if ((t == 1 && nf >= 1 && all_conv) || (t >= 2 && nf == prev && all_conv)) {
+      converged = true;
+      break;
+    }
+    prev = nf;
+    if (h->opts.driver == 1) {
+      launch_copy_cols(n, k, h->Xh, n, h->Yb, n, s);                         // Y <- Ritz vectors
+    } else {
+      pc *= 2;                                                               // line 13
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st != IE_OK) return st;
+  // order: filtered first, each group by |lambda - c|
+  std::vector<int> ord(k);
+  std::iota(ord.begin(), ord.end(), 0);
+  auto dist = [&](int i) {
+    return (std::isfinite(lam[i].real()) && std::isfinite(lam[i].imag()))
+               ? std::abs(lam[i] - h->center)
+               : std::numeric_limits<double>::infinity();
+  };
+  std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) {
+    if (filt[a] != filt[b]) return filt[a] > filt[b];
+    return dist(a) < dist(b);
+  });
+  CK(cudaMemcpyAsync(h->d_perm, ord.data(), sizeof(int) * k, cudaMemcpyHostToDevice, s));
+  const bool xdev = is_device_ptr(X_any);
+  cplx* Xo = xdev ? (cplx*)X_any : h->Ub;
+  const int64_t ldXo = xdev ? ldx : n;
+  launch_permute_cols(n, k, h->Xh, n, h->d_perm, Xo, ldXo, s);
+  if (!xdev) CKS(stage_out(h, Xo, ldXo, k, X_any, ldx, s));
+  CKS(check_status(h, s));
+  for (int i = 0; i < k; ++i) {
+    const zc l = lam[ord[i]];
+    h_lambda[i].re = l.real();
+    h_lambda[i].im = l.imag();
+    if (h_rho) h_rho[i] = rho[ord[i]];
+    if (h_e) h_e[i] = e[ord[i]];
+  }
+  *n_found = nf;
+  S.converged = converged ? 1 : 0;
+  S.g_columns = h->g_columns;
+  if (stats) *stats = S;
+  (void)any_noconv;
+  return converged ? IE_OK : IE_ERR_NOCONV;
+}
+
+// ------------------------------ introspection -----------------------------------------------
+extern "C" ie_status ie_get_coeffs(ie_handle h, ie_complex* h_poles, ie_complex* h_weights,
+                                   ie_complex* h_shifts, ie_complex* h_cweights, int32_t* n_shift,
+                                   double* odd_coef) {
+  if (!h) return IE_ERR_ARG;
+  for (int i = 0; i < h->q; ++i) {
+    if (h_poles) { h_poles[i].re = h->poles[i].real(); h_poles[i].im = h->poles[i].imag(); }
+    if (h_weights) { h_weights[i].re = h->weights[i].real(); h_weights[i].im = h->weights[i].imag(); }
+  }
+  std::vector<zc> sh, cw;
+  double odd = 0;
+  outer_coeffs(h->p, sh, cw, odd);
+  for (size_t j = 0; j < sh.size(); ++j) {
+    if (h_shifts) { h_shifts[j].re = sh[j].real(); h_shifts[j].im = sh[j].imag(); }
+    if (h_cweights) { h_cweights[j].re = cw[j].real(); h_cweights[j].im = cw[j].imag(); }
+  }
+  if (n_shift) *n_shift = (int32_t)sh.size();
+  if (odd_coef) *odd_coef = odd;
+  return IE_OK;
+}
+
+extern "C" ie_status ie_get_factor(ie_handle h, int32_t pole, ie_complex* h_ab, int32_t* h_ipiv,
+                                   int32_t* kl, int32_t* ldab) {
+  if (!h || pole < 0 || pole >= h->q) return IE_ERR_ARG;
+  if (kl) *kl = h->kl;
+  if (ldab) *ldab = h->ldab;
+  if (h_ab)
+    CK(cudaMemcpy(h_ab, h->AB + (int64_t)pole * h->n_pad * h->ldab,
+                  sizeof(cplx) * (size_t)h->n * h->ldab, cudaMemcpyDeviceToHost));
+  if (h_ipiv) {
+    CK(cudaMemcpy(h_ipiv, h->piv + (int64_t)pole * h->n_pad, sizeof(int) * (size_t)h->n,
+                  cudaMemcpyDeviceToHost));
+    for (int64_t i = 0; i < h->n; ++i) h_ipiv[i] += 1;   // LAPACK 1-based
+  }
+  return IE_OK;
+}
+
+extern "C" ie_status ie_get_stats(ie_handle h, ie_stats* out) {
+  if (!h || !out) return IE_ERR_ARG;
+  *out = h->stats;
+  out->g_columns = h->g_columns;
+  return IE_OK;
+}

@@ -1,0 +1,164 @@
+// Internal declarations shared by the CUDA translation units of libie.
+// Complex arithmetic is complex128 held in double2 (x = real, y = imaginary).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <vector>
+
+#include "../../include/ie.h"
+
+typedef double2 cplx;
+
+#define IE_HD __host__ __device__ __forceinline__
+
+IE_HD cplx cmk(double re, double im) { return make_double2(re, im); }
+IE_HD cplx cadd(cplx a, cplx b) { return make_double2(a.x + b.x, a.y + b.y); }
+IE_HD cplx csub(cplx a, cplx b) { return make_double2(a.x - b.x, a.y - b.y); }
+IE_HD cplx cscale(cplx a, double s) { return make_double2(a.x * s, a.y * s); }
+IE_HD cplx cconj(cplx a) { return make_double2(a.x, -a.y); }
+IE_HD cplx cmul(cplx a, cplx b) {
+  return make_double2(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
+}
+// c + a*b
+IE_HD cplx cfma(cplx a, cplx b, cplx c) {
+  return make_double2(fma(a.x, b.x, fma(-a.y, b.y, c.x)), fma(a.x, b.y, fma(a.y, b.x, c.y)));
+}
+// c - a*b
+IE_HD cplx cfms(cplx a, cplx b, cplx c) {
+  return make_double2(fma(-a.x, b.x, fma(a.y, b.y, c.x)), fma(-a.x, b.y, fma(-a.y, b.x, c.y)));
+}
+// c + conj(a)*b
+IE_HD cplx cfma_conj(cplx a, cplx b, cplx c) {
+  return make_double2(fma(a.x, b.x, fma(a.y, b.y, c.x)), fma(a.x, b.y, fma(-a.y, b.x, c.y)));
+}
+IE_HD double cabs2(cplx a) { return fma(a.x, a.x, a.y * a.y); }
+IE_HD double cabs1(cplx a) { return fabs(a.x) + fabs(a.y); }
+IE_HD double cabsv(cplx a) { return hypot(a.x, a.y); }
+// a / b by Smith's algorithm (R. L. Smith, CACM 5(8), 1962).
+IE_HD cplx cdiv(cplx a, cplx b) {
+  if (fabs(b.x) >= fabs(b.y)) {
+    double r = b.y / b.x, d = b.x + b.y * r;
+    return make_double2((a.x + a.y * r) / d, (a.y - a.x * r) / d);
+  } else {
+    double r = b.x / b.y, d = b.y + b.x * r;
+    return make_double2((a.x * r + a.y) / d, (a.y * r - a.x) / d);
+  }
+}
+IE_HD cplx crcp(cplx b) { return cdiv(make_double2(1.0, 0.0), b); }
+
+// ---- status words written by kernels (device memory, one int each) ----
+enum {
+  ST_SINGULAR = 0,   // first zero pivot column + 1 over all poles (0 = none)
+  ST_TIMEOUT = 1,    // nonzero if a bounded wait gave up
+  ST_ABORT = 2,      // set to make cooperating CTAs leave early
+  ST_COUNT = 8
+};
+
+#define IE_MAX_DIAG 16
+
+// Bounded-wait limit for device spin loops, in nanoseconds of %globaltimer.
+#define IE_WAIT_NS (2000ull * 1000ull * 1000ull)
+
+__device__ __forceinline__ unsigned long long ie_globaltimer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// ---------------- kernel launchers (defined in ie_band.cu / ie_krylov.cu / ie_hsrr.cu) -------
+struct DiaDev {
+  int64_t n;
+  int ndiag;
+  int64_t off[IE_MAX_DIAG];
+  const cplx* A;  // ndiag * n
+  const cplx* B;
+};
+
+// Y[:, c] = (alpha_A A + alpha_B B) X[:, c] for c < k; X column c starts at X + xoff[c]
+// when xoff != nullptr, else at X + c*ldx. Y column c at Y + c*ldy.
+void launch_spmv(const DiaDev& P, cplx alphaA, cplx alphaB, const cplx* X, int64_t ldx,
+                 const int64_t* xoff, int k, cplx* Y, int64_t ldy, cudaStream_t s);
+// Assemble K_i = p_i B - A into LAPACK band storage for all q poles (columns >= n zeroed).
+void launch_assemble(const DiaDev& P, const cplx* d_poles, int q, int kl, int ldab,
+                     int64_t n_pad, cplx* AB, cudaStream_t s);
+// Batched band LU with partial pivoting, all q poles in one cooperative launch.
+cudaError_t launch_band_lu(int q, int64_t n, int kl, int ldab, int64_t n_pad, cplx* AB,
+                           int* piv, cplx* dinv, unsigned* bar, int* status, cudaStream_t s,
+                           int* ctas_per_pole);
+// Forward (P, L) then backward (U) band solves for all q poles and k RHS columns;
+// Xp[i] (n x k, ld = ldx, pole stride xstride) = w_i K_i^{-1} RHS.
+cudaError_t launch_band_solve(int q, int64_t n, int kl, int ldab, int64_t n_pad, const cplx* AB,
+                              const int* piv, const cplx* dinv, const cplx* d_weights,
+                              const cplx* RHS, int64_t ldr, int k, cplx* Xp, int64_t ldx,
+                              int64_t xstride, int* status, cudaStream_t s);
+// GV[:, c] = sum_i Xp[i][:, c]
+void launch_pole_sum(int q, int64_t n, int k, const cplx* Xp, int64_t ldx, int64_t xstride,
+                     cplx* GV, int64_t ldg, cudaStream_t s);
+void launch_norm1_cols(const DiaDev& P, int which, double* d_out, double* d_scratch,
+                       cudaStream_t s);
+
+// ---- Krylov (ie_krylov.cu) ----
+struct KrylovDev {
+  int64_t n;
+  int m_max;
+  cplx* V;       // kmax * (m_max+1) * n ; column c basis at V + c*(m_max+1)*n
+  cplx* H;       // kmax * (m_max+1) * m_max ; H_c col-major ld m_max+1
+  double* beta;  // kmax
+  int* jc;       // kmax : Arnoldi steps taken per column
+  int* brk;      // kmax : breakdown flag
+};
+
+// Column norms of an n x k block (partial sums in scratch, result in d_out[k]).
+void launch_colnorm2(int64_t n, int k, const cplx* X, int64_t ldx, double* d_out,
+                     double* d_scratch, cudaStream_t s);
+// Start Krylov spaces: beta_c = ||Yt_c||, V_c[:,0] = Yt_c / beta_c, jc = 0.
+void launch_krylov_start(const KrylovDev& K, int k, const cplx* Yt, int64_t ldy, double* scratch,
+                         cudaStream_t s);
+// Offsets of V_c[:, jc[c]] for the active list (for the SpMV gather).
+void launch_active_offsets(const KrylovDev& K, const int* act, int kact, int64_t* d_off,
+                           cudaStream_t s);
+// One Arnoldi step (CGS2) for the active columns; W (n x kact) is G applied to v_j.
+void launch_arnoldi_cgs2(const KrylovDev& K, const int* act, int kact, cplx* W, int64_t ldw,
+                         cplx* hbuf, double* scratch, cudaStream_t s);
+// Multi-shift Givens update over H columns [jc_from, jc_to) per (column, shift);
+// writes per-column max relative residual into d_res[act index].
+void launch_givens(const KrylovDev& K, const int* act, int kact, const cplx* d_shifts,
+                   int nshift, cplx* rot_c, cplx* rot_s, cplx* gvec, int from_zero,
+                   double* d_res, cudaStream_t s);
+// Final combine: U_c = V_c (sum_l wt_l y_l) + odd*beta_c v_0 for all k columns.
+void launch_krylov_combine(const KrylovDev& K, int k, const cplx* d_shifts, const cplx* d_wts,
+                           int nshift, double odd, cplx* Rscratch, cplx* zbuf, cplx* U,
+                           int64_t ldu, cudaStream_t s);
+
+// ---- block orthogonalisation / HSRR (ie_hsrr.cu) ----
+// In-place CGS2 orthonormalisation of the n x k block Q with the rank guard;
+// replaced columns get counter-based random vectors from (seed, salt, column).
+void launch_orth_cgs2(int64_t n, int k, cplx* Q, int64_t ldq, uint64_t seed, uint32_t salt,
+                      cplx* hbuf, double* scratch, int* flags, cudaStream_t s);
+// C (k x k, col-major ld k) = W^H Y for n x k blocks.
+void launch_gram(int64_t n, int k, const cplx* W, int64_t ldw, const cplx* Y, int64_t ldy,
+                 cplx* C, cplx* scratch, cudaStream_t s);
+// Complex QZ of (Ah, Bh) (k x k) + right eigenvectors: alpha, beta (k each),
+// M = P_R V_R (k x k col-major). One CTA.
+cudaError_t launch_qz(int k, cplx* Ah, cplx* Bh, cplx* Z, cplx* alpha, cplx* beta, cplx* M,
+                      int* status, cudaStream_t s);
+// Y (n x k) = X (n x k) * M (k x k).
+void launch_gemm_small(int64_t n, int k, const cplx* X, int64_t ldx, const cplx* M, cplx* Y,
+                       int64_t ldy, cudaStream_t s);
+// X[:, c] /= ||X[:, c]||.
+void launch_normalize_cols(int64_t n, int k, cplx* X, int64_t ldx, double* scratch,
+                           cudaStream_t s);
+// Residual norms per column: out[3c+0] = ||A x - lam B x||^2, out[3c+1] = ||B x||^2,
+// out[3c+2] = ||x||^2.
+void launch_residual_norms(const DiaDev& P, int k, const cplx* X, int64_t ldx, const cplx* lam,
+                           double* d_out, double* scratch, cudaStream_t s);
+// Y[:, c] = X[:, perm[c]]
+void launch_permute_cols(int64_t n, int k, const cplx* X, int64_t ldx, const int* perm, cplx* Y,
+                         int64_t ldy, cudaStream_t s);
+// Counter-based random complex Gaussian block (SplitMix64 + Box-Muller).
+void launch_random_block(int64_t n, int k, cplx* X, int64_t ldx, uint64_t seed, uint32_t salt,
+                         cudaStream_t s);
+// generic copies
+void launch_copy_cols(int64_t n, int k, const cplx* X, int64_t ldx, cplx* Y, int64_t ldy,
+                      cudaStream_t s);

@@ -1,0 +1,244 @@
+"""ctypes binding of the C ABI declared in include/ie.h (same names, argument
+marshalling only). Every computation runs in libie.so's CUDA kernels; there is no
+CPU fallback: importing this module does not load the library, the first call does,
+and it raises if the library has not been built.
+
+Pointer arguments accept torch tensors (device memory, complex128) or numpy arrays
+(host memory, complex128). Blocks are n x k column-major: pass a tensor/array whose
+first dimension is n and whose row stride is 1 (for example `t.T` of a (k, n)
+contiguous tensor, or `np.asfortranarray`); the leading dimension is read from the
+column stride.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libie.so")
+
+IE_OK, IE_ERR_ARG, IE_ERR_CUDA, IE_ERR_OOM, IE_ERR_SINGULAR, IE_ERR_NOCONV, IE_ERR_BREAKDOWN, IE_ERR_TIMEOUT = range(8)
+
+
+class ie_complex(C.Structure):
+    _fields_ = [("re", C.c_double), ("im", C.c_double)]
+
+
+class ie_pencil(C.Structure):
+    _fields_ = [("n", C.c_int64), ("ndiag", C.c_int32), ("h_offsets", C.POINTER(C.c_int64)),
+                ("d_A_dia", C.c_void_p), ("d_B_dia", C.c_void_p)]
+
+
+class ie_opts(C.Structure):
+    _fields_ = [("k", C.c_int32), ("driver", C.c_int32), ("m_max", C.c_int32),
+                ("max_outer", C.c_int32), ("tau_g", C.c_double), ("tau", C.c_double),
+                ("gmres_tol", C.c_double), ("sigma_is_center", C.c_int32),
+                ("sigma_re", C.c_double), ("sigma_im", C.c_double), ("seed", C.c_uint64)]
+
+
+class ie_stats(C.Structure):
+    _fields_ = [("outer_iters", C.c_int32), ("n_found", C.c_int32), ("p_final", C.c_int32),
+                ("gmres_iters_max", C.c_int32), ("gmres_iters_min", C.c_int32),
+                ("converged", C.c_int32), ("g_columns", C.c_int64), ("t_factor_ms", C.c_double),
+                ("t_filter_ms", C.c_double), ("t_hsrr_ms", C.c_double),
+                ("max_rho_found", C.c_double)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+EXPORTS = ["ie_opts_default", "ie_create", "ie_destroy", "ie_status_str", "ie_filter_apply",
+           "ie_apply_G", "ie_hsrr", "ie_solve", "ie_spmv", "ie_get_coeffs", "ie_get_factor",
+           "ie_get_stats"]
+
+_lib = None
+_vp, _i32, _i64, _dp = C.c_void_p, C.c_int32, C.c_int64, C.POINTER(C.c_double)
+
+
+def load():
+    """Loads libie.so (raises if it is missing: there is no fallback path)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"libie.so not built ({LIB_PATH}); run __graft_entry__.build()")
+    L = C.CDLL(LIB_PATH)
+    L.ie_opts_default.argtypes = [C.POINTER(ie_opts)]
+    L.ie_opts_default.restype = None
+    L.ie_status_str.argtypes = [C.c_int]
+    L.ie_status_str.restype = C.c_char_p
+    L.ie_create.argtypes = [C.POINTER(ie_pencil), ie_complex, C.c_double, _i32, _i32,
+                            C.POINTER(ie_opts), _vp, C.POINTER(_vp)]
+    L.ie_destroy.argtypes = [_vp]
+    L.ie_filter_apply.argtypes = [_vp, _vp, _i64, _i32, _vp, _i64, _vp]
+    L.ie_apply_G.argtypes = [_vp, _vp, _i64, _i32, _vp, _i64, _vp]
+    L.ie_hsrr.argtypes = [_vp, _vp, _i64, _i32, _vp, _vp, _i64, _vp, _vp, _vp]
+    L.ie_solve.argtypes = [_vp, _vp, _i64, _vp, _vp, _i64, _vp, _vp, C.POINTER(_i32),
+                           C.POINTER(ie_stats), _vp]
+    L.ie_spmv.argtypes = [_vp, _i32, _vp, _i64, _i32, _vp, _i64, _vp]
+    L.ie_get_coeffs.argtypes = [_vp, _vp, _vp, _vp, _vp, C.POINTER(_i32), _dp]
+    L.ie_get_factor.argtypes = [_vp, _i32, _vp, _vp, C.POINTER(_i32), C.POINTER(_i32)]
+    L.ie_get_stats.argtypes = [_vp, C.POINTER(ie_stats)]
+    for f in EXPORTS:
+        if f not in ("ie_opts_default", "ie_status_str"):
+            getattr(L, f).restype = C.c_int
+    _lib = L
+    return L
+
+
+class IeError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        super().__init__(f"{where}: {ie_status_str(status)}")
+        self.status = status
+
+
+def _stream(stream):
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+        except Exception:
+            pass
+        return None
+    if isinstance(stream, int):
+        return C.c_void_p(stream)
+    return C.c_void_p(stream.cuda_stream)
+
+
+def _block(x):
+    """(pointer, ld, rows, cols) of an n x k column-major complex128 block."""
+    if x is None:
+        return None, 0, 0, 0
+    try:
+        import torch
+        if isinstance(x, torch.Tensor):
+            if x.dtype != torch.complex128:
+                raise TypeError("complex128 tensor expected")
+            if x.dim() == 1:
+                return C.c_void_p(x.data_ptr()), x.shape[0], x.shape[0], 1
+            if x.stride(0) != 1:
+                raise ValueError("column-major block expected (row stride 1)")
+            ld = x.stride(1) if x.shape[1] > 1 else x.shape[0]
+            return C.c_void_p(x.data_ptr()), ld, x.shape[0], x.shape[1]
+    except ImportError:
+        pass
+    if isinstance(x, np.ndarray):
+        if x.dtype != np.complex128:
+            raise TypeError("complex128 array expected")
+        if x.ndim == 1:
+            return C.c_void_p(x.ctypes.data), x.shape[0], x.shape[0], 1
+        if x.strides[0] != 16:
+            raise ValueError("column-major block expected (Fortran order)")
+        ld = x.strides[1] // 16 if x.shape[1] > 1 else x.shape[0]
+        return C.c_void_p(x.ctypes.data), ld, x.shape[0], x.shape[1]
+    raise TypeError(f"unsupported block type {type(x)}")
+
+
+def _vec(x):
+    if x is None:
+        return None
+    if isinstance(x, np.ndarray):
+        return C.c_void_p(x.ctypes.data)
+    return C.c_void_p(x.data_ptr())
+
+
+def ie_status_str(status: int) -> str:
+    return load().ie_status_str(int(status)).decode()
+
+
+def ie_opts_default(**overrides) -> ie_opts:
+    o = ie_opts()
+    load().ie_opts_default(C.byref(o))
+    for k_, v in overrides.items():
+        setattr(o, k_, v)
+    return o
+
+
+def ie_create(n, offsets, A_dia, B_dia, center, radius, p, q, opts=None, stream=None):
+    """Returns (status, handle). A_dia, B_dia: (ndiag, n) complex128 (device tensor or host array)."""
+    L = load()
+    offs = np.ascontiguousarray(np.asarray(offsets, dtype=np.int64))
+    pen = ie_pencil(int(n), len(offs), offs.ctypes.data_as(C.POINTER(C.c_int64)), _vec(A_dia),
+                    _vec(B_dia))
+    h = C.c_void_p()
+    o = opts if opts is not None else ie_opts_default()
+    st = L.ie_create(C.byref(pen), ie_complex(complex(center).real, complex(center).imag),
+                     float(radius), int(p), int(q), C.byref(o), _stream(stream), C.byref(h))
+    return st, h
+
+
+def ie_destroy(h):
+    return load().ie_destroy(h)
+
+
+def ie_filter_apply(h, Y, U, stream=None):
+    py, ldy, n, k = _block(Y)
+    pu, ldu, _, _ = _block(U)
+    return load().ie_filter_apply(h, py, ldy, k, pu, ldu, _stream(stream))
+
+
+def ie_apply_G(h, V, GV, stream=None):
+    pv, ldv, n, k = _block(V)
+    pg, ldg, _, _ = _block(GV)
+    return load().ie_apply_G(h, pv, ldv, k, pg, ldg, _stream(stream))
+
+
+def ie_spmv(h, which, X, Y, stream=None):
+    px, ldx, n, k = _block(X)
+    py, ldy, _, _ = _block(Y)
+    return load().ie_spmv(h, int(which), px, ldx, k, py, ldy, _stream(stream))
+
+
+def ie_hsrr(h, U, X=None, stream=None):
+    """Returns (status, lambda (k,), e (k,), rho (k,)); Ritz vectors into X when given."""
+    pu, ldu, n, k = _block(U)
+    px, ldx, _, _ = _block(X)
+    lam = np.zeros(k, dtype=np.complex128)
+    e = np.zeros(k)
+    rho = np.zeros(k)
+    st = load().ie_hsrr(h, pu, ldu, k, _vec(lam), px, ldx if X is not None else 0, _vec(e),
+                        _vec(rho), _stream(stream))
+    return st, lam, e, rho
+
+
+def ie_solve(h, Y0, X, k, stream=None):
+    """Returns (status, lambda (k,), rho (k,), e (k,), n_found, stats dict)."""
+    p0, ld0, _, _ = _block(Y0)
+    px, ldx, _, _ = _block(X)
+    lam = np.zeros(k, dtype=np.complex128)
+    rho = np.zeros(k)
+    e = np.zeros(k)
+    nf = C.c_int32()
+    stt = ie_stats()
+    st = load().ie_solve(h, p0, ld0 if Y0 is not None else 0, _vec(lam), px, ldx, _vec(rho),
+                         _vec(e), C.byref(nf), C.byref(stt), _stream(stream))
+    return st, lam, rho, e, nf.value, stt.as_dict()
+
+
+def ie_get_coeffs(h, p, q):
+    poles = np.zeros(q, dtype=np.complex128)
+    w = np.zeros(q, dtype=np.complex128)
+    s = np.zeros(max(p, 1), dtype=np.complex128)
+    c = np.zeros(max(p, 1), dtype=np.complex128)
+    ns = C.c_int32()
+    odd = C.c_double()
+    st = load().ie_get_coeffs(h, _vec(poles), _vec(w), _vec(s), _vec(c), C.byref(ns), C.byref(odd))
+    return st, poles, w, s[: ns.value], c[: ns.value], odd.value
+
+
+def ie_get_factor(h, pole, n, ldab):
+    ab = np.zeros((n, ldab), dtype=np.complex128)        # row j = band column j
+    ipiv = np.zeros(n, dtype=np.int32)
+    kl = C.c_int32()
+    ld = C.c_int32()
+    st = load().ie_get_factor(h, int(pole), _vec(ab), _vec(ipiv), C.byref(kl), C.byref(ld))
+    return st, np.asfortranarray(ab.T), ipiv, kl.value
+
+
+def ie_get_stats(h):
+    s = ie_stats()
+    st = load().ie_get_stats(h, C.byref(s))
+    return st, s.as_dict()

@@ -1,0 +1,82 @@
+"""CPU checks of the C-ABI library: it builds for sm_103a, loads without a GPU,
+and exports every function include/ie.h declares; the binding's struct layouts
+match the header's field lists."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "ie.h")
+
+
+def declared_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(ie_[A-Za-z_0-9]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2310_18043_gb300 import build as b
+    path = b.build()
+    return ctypes.CDLL(path)
+
+
+def test_header_declares_the_boundary():
+    fns = declared_functions()
+    for f in ["ie_create", "ie_filter_apply", "ie_solve", "ie_destroy", "ie_status_str",
+              "ie_apply_G", "ie_hsrr", "ie_spmv", "ie_get_coeffs", "ie_get_factor",
+              "ie_get_stats", "ie_opts_default"]:
+        assert f in fns
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for f in declared_functions():
+        assert hasattr(lib, f), f"{f} not exported"
+
+
+def test_binding_knows_every_export():
+    import paper_2310_18043_gb300.ie as ie
+    assert sorted(ie.EXPORTS) == declared_functions()
+
+
+def test_struct_layouts_match_header():
+    import paper_2310_18043_gb300.ie as ie
+    src = open(HEADER).read()
+
+    def fields(name):
+        body = re.search(r"typedef struct \{([^{}]*)\}\s*" + name + ";", src).group(1)
+        body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
+        out = []
+        for decl in body.split(";"):
+            decl = decl.strip()
+            if not decl:
+                continue
+            for piece in decl.split(","):
+                out.append(re.findall(r"[A-Za-z_]\w*", piece)[-1])
+        return out
+
+    assert [f for f, _ in ie.ie_opts._fields_] == fields("ie_opts")
+    assert [f for f, _ in ie.ie_stats._fields_] == fields("ie_stats")
+    assert [f for f, _ in ie.ie_pencil._fields_] == fields("ie_pencil")
+
+
+def test_status_strings_and_defaults(lib):
+    import paper_2310_18043_gb300.ie as ie
+    assert ie.ie_status_str(ie.IE_OK) == "IE_OK"
+    assert "NOCONV" in ie.ie_status_str(ie.IE_ERR_NOCONV)
+    o = ie.ie_opts_default()
+    assert (o.k, o.driver, o.m_max, o.max_outer) == (16, 1, 100, 10)
+    assert (o.tau_g, o.tau, o.gmres_tol, o.sigma_is_center) == (1e-2, 1e-10, 1e-12, 1)
+
+
+def test_no_oracle_in_product_path():
+    """The product package never imports the oracle."""
+    pkg = os.path.join(ROOT, "paper_2310_18043_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h")):
+                txt = open(os.path.join(dirpath, f)).read()
+                assert "import oracle" not in txt and "from oracle" not in txt, f

@@ -1,0 +1,327 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 CPU oracle on the
+same seeded inputs, and against the reference eigenvalues in tests/golden.
+
+Tolerances: SpMV 1e-14 (same products, different summation order); band LU
+checked as a LAPACK zgbtrf factorisation (same pivots, entries to 1e-12); G(V)
+1e-11 relative (direct solves, rounding of K^{-1} amplified by its condition);
+filtered block 1e-9 relative (both sides stop GMRES at 1e-12 relative residual);
+eigenvalues in D 1e-10 relative, rho <= 1e-10, identical counts.
+"""
+import numpy as np
+import pytest
+
+import ie_inputs
+from oracle import coeffs, hsrr as ohsrr, inner, msgmres, pencil as opencil
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ie():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2310_18043_gb300 import build as b
+    b.build()
+    import paper_2310_18043_gb300.ie as ie_
+    return ie_
+
+
+DEV = "cuda:0"
+
+
+def dblock(a):
+    """host (n, k) -> device column-major tensor"""
+    a = np.asarray(a, dtype=np.complex128)
+    if a.ndim == 1:
+        a = a[:, None]
+    return torch.from_numpy(np.ascontiguousarray(a.T)).to(DEV).T
+
+
+def dzeros(n, k):
+    return torch.zeros((k, n), dtype=torch.complex128, device=DEV).T
+
+
+class Case:
+    def __init__(self, ie, name, **over):
+        w = dict(ie_inputs.load_workload(name))
+        w.update(over)
+        self.w = w
+        self.pen = ie_inputs.make_pencil(w["m"], w["seed"])
+        self.n = self.pen.n
+        self.A, self.B = opencil.pencil_matrices(self.pen)
+        opts = ie.ie_opts_default(k=w["k"], driver=w.get("driver", 1), seed=0)
+        for key in ("m_max", "max_outer", "gmres_tol"):
+            if key in w:
+                setattr(opts, key, w[key])
+        self.Ad = torch.from_numpy(self.pen.A_dia).to(DEV)
+        self.Bd = torch.from_numpy(self.pen.B_dia).to(DEV)
+        st, self.h = ie.ie_create(self.n, self.pen.offsets, self.Ad, self.Bd, w["center"],
+                                  w["radius"], w["p"], w["q"], opts)
+        assert st == ie.IE_OK, ie.ie_status_str(st)
+        self.ie = ie
+
+    def close(self):
+        self.ie.ie_destroy(self.h)
+
+
+@pytest.fixture(scope="module")
+def c1(ie):
+    c = Case(ie, "c1_m24")
+    yield c
+    c.close()
+
+
+@pytest.fixture(scope="module")
+def r1(ie):
+    c = Case(ie, "r1_m37")
+    yield c
+    c.close()
+
+
+def golden_eigs(w):
+    return np.array(w["eig_in_disk_re"]) + 1j * np.array(w["eig_in_disk_im"])
+
+
+def match_eigs(got, ref, rel=1e-10):
+    got = np.asarray(got)
+    assert len(got) == len(ref)
+    d = np.abs(got[:, None] - ref[None, :])
+    j = np.argmin(d, axis=1)
+    assert sorted(j) == list(range(len(ref))), "not a one-to-one match"
+    err = np.max(np.min(d, axis=1) / np.abs(ref[j]))
+    assert err < rel, f"eigenvalue rel err {err:.3e}"
+    return err
+
+
+# ---------------------------------------------------------------- a1: coefficients
+@pytest.mark.parametrize("name", ["c1_m24", "r1_m37"])
+def test_coefficients_match_oracle(ie, name):
+    c = Case(ie, name)
+    try:
+        w = c.w
+        st, poles, wts, sh, cw, odd = ie.ie_get_coeffs(c.h, w["p"], w["q"])
+        assert st == ie.IE_OK
+        rp, rw = coeffs.trapezoid_poles_weights(w["center"], w["radius"], w["q"])
+        rs, rc, rodd = coeffs.outer_shifts_weights(w["p"])
+        assert np.allclose(poles, rp, rtol=1e-15, atol=1e-12)
+        assert np.allclose(wts, rw, rtol=1e-14, atol=1e-15)
+        assert np.allclose(sh, rs, rtol=1e-14, atol=1e-15)
+        assert np.allclose(cw, rc, rtol=1e-14, atol=1e-15)
+        assert odd == rodd
+    finally:
+        c.close()
+
+
+# ---------------------------------------------------------------- K3: SpMV
+def test_spmv_matches_csr(ie, r1):
+    X = ie_inputs.random_block(r1.n, 5, seed=3)
+    for which, M in ((0, r1.A), (1, r1.B)):
+        Yd = dzeros(r1.n, 5)
+        assert ie.ie_spmv(r1.h, which, dblock(X), Yd) == ie.IE_OK
+        ref = M @ X
+        err = np.linalg.norm(Yd.cpu().numpy() - ref) / np.linalg.norm(ref)
+        assert err < 1e-14
+
+
+# ---------------------------------------------------------------- a2-a3: band LU
+@pytest.mark.parametrize("fixture", ["c1", "r1"])
+def test_band_lu_is_lapack_gbtrf(ie, fixture, request):
+    from scipy.linalg import lapack
+    c = request.getfixturevalue(fixture)
+    n, m = c.n, c.pen.half_bw
+    ldab = 3 * m + 1
+    poles, _ = coeffs.trapezoid_poles_weights(c.w["center"], c.w["radius"], c.w["q"])
+    for i, pole in enumerate(poles):
+        st, ab, ipiv, kl = ie.ie_get_factor(c.h, i, n, ldab)
+        assert st == ie.IE_OK and kl == m
+        K = (pole * c.B - c.A).toarray()
+        # LAPACK's own factorisation of the same band matrix
+        band = np.zeros((ldab, n), dtype=np.complex128, order="F")
+        for j in range(n):
+            for r in range(max(0, j - m), min(n, j + m + 1)):
+                band[2 * m + r - j, j] = K[r, j]
+        lu, piv_ref, info = lapack.zgbtrf(band, m, m)
+        assert info == 0
+        assert np.array_equal(ipiv, piv_ref + 1), "pivot sequence differs from zgbtrf"
+        scale = np.abs(lu).max()
+        assert np.max(np.abs(ab - lu)) <= 1e-12 * scale
+        # and it solves K x = b
+        b = ie_inputs.random_block(n, 2, seed=i)
+        x, info = lapack.zgbtrs(ab, m, m, b, ipiv - 1)
+        assert info == 0
+        res = np.linalg.norm(K @ x - b) / (np.linalg.norm(K, 1) * np.linalg.norm(x))
+        assert res < 1e-14
+
+
+# ---------------------------------------------------------------- a4: inner operator G
+@pytest.mark.parametrize("name,k", [("c1_m24", 16), ("r1_m37", 11), ("m1_m64", 24)])
+def test_apply_G_matches_oracle(ie, name, k):
+    c = Case(ie, name)
+    try:
+        V = ie_inputs.random_block(c.n, k, seed=5)
+        GVd = dzeros(c.n, k)
+        assert ie.ie_apply_G(c.h, dblock(V), GVd) == ie.IE_OK
+        G = inner.InnerOperator(c.A, c.B, c.w["center"], c.w["radius"], c.w["q"])
+        ref = G.apply(V)
+        got = GVd.cpu().numpy()
+        err = np.linalg.norm(got - ref, axis=0) / np.linalg.norm(ref, axis=0)
+        assert err.max() < 1e-11, err.max()
+        st, stats = ie.ie_get_stats(c.h)
+        assert stats["g_columns"] == k
+    finally:
+        c.close()
+
+
+def test_apply_G_one_column_and_ragged_ld(ie, r1):
+    """k = 1 and a leading dimension larger than n (views into a bigger buffer)."""
+    V = ie_inputs.random_block(r1.n, 3, seed=8)
+    big = torch.zeros((3, r1.n + 13), dtype=torch.complex128, device=DEV)
+    big[:, : r1.n] = torch.from_numpy(np.ascontiguousarray(V.T)).to(DEV)
+    Vd = big.T[: r1.n]
+    out = torch.zeros((3, r1.n + 7), dtype=torch.complex128, device=DEV)
+    Gd = out.T[: r1.n]
+    assert ie.ie_apply_G(r1.h, Vd[:, :1], Gd[:, :1]) == ie.IE_OK
+    assert ie.ie_apply_G(r1.h, Vd, Gd) == ie.IE_OK
+    G = inner.InnerOperator(r1.A, r1.B, r1.w["center"], r1.w["radius"], r1.w["q"])
+    ref = G.apply(V)
+    assert np.linalg.norm(Gd.cpu().numpy() - ref) / np.linalg.norm(ref) < 1e-11
+    assert torch.all(out[:, r1.n:] == 0)
+
+
+# ---------------------------------------------------------------- a5-a6: filter
+@pytest.mark.parametrize("fixture", ["c1", "r1"])
+def test_filter_apply_matches_oracle(ie, fixture, request):
+    c = request.getfixturevalue(fixture)
+    k = c.w["k"]
+    Y = ie_inputs.orthonormal_random_block(c.n, k, seed=2)
+    Ud = dzeros(c.n, k)
+    assert ie.ie_filter_apply(c.h, dblock(Y), Ud) == ie.IE_OK
+    G = inner.InnerOperator(c.A, c.B, c.w["center"], c.w["radius"], c.w["q"])
+    ref, st = msgmres.filter_apply(G, Y, c.w["p"], tol=1e-12, m_max=100, return_stats=True)
+    got = Ud.cpu().numpy()
+    err = np.linalg.norm(got - ref) / np.linalg.norm(ref)
+    assert err < 1e-9, err
+    # the composite filter equals the p*q-pole simple rule (Thm 2)
+    full = inner.InnerOperator(c.A, c.B, c.w["center"], c.w["radius"], c.w["p"] * c.w["q"]).apply(Y)
+    assert np.linalg.norm(got - full) / np.linalg.norm(full) < 1e-9
+    _, stats = ie.ie_get_stats(c.h)
+    assert stats["gmres_iters_max"] == max(st["gmres_iters"])
+
+
+def test_filter_host_buffers_equal_device(ie, c1):
+    k = c1.w["k"]
+    Y = np.asfortranarray(ie_inputs.orthonormal_random_block(c1.n, k, seed=4))
+    U_host = np.zeros((c1.n, k), dtype=np.complex128, order="F")
+    assert ie.ie_filter_apply(c1.h, Y, U_host) == ie.IE_OK
+    Ud = dzeros(c1.n, k)
+    assert ie.ie_filter_apply(c1.h, dblock(Y), Ud) == ie.IE_OK
+    assert np.array_equal(U_host, Ud.cpu().numpy())
+
+
+# ---------------------------------------------------------------- a7: HSRR
+def test_hsrr_matches_oracle(ie, c1):
+    k = c1.w["k"]
+    Y = ie_inputs.orthonormal_random_block(c1.n, k, seed=6)
+    G = inner.InnerOperator(c1.A, c1.B, c1.w["center"], c1.w["radius"], c1.w["q"])
+    U = msgmres.filter_apply(G, Y, c1.w["p"], tol=1e-12, m_max=100)
+    Xd = dzeros(c1.n, k)
+    st, lam, e, rho = ie.ie_hsrr(c1.h, dblock(U), Xd)
+    assert st == ie.IE_OK
+    nA, nB = opencil.norm1(c1.A), opencil.norm1(c1.B)
+    ref = ohsrr.hsrr(c1.A, c1.B, U, c1.w["center"], c1.w["center"], c1.w["radius"], nA, nB)
+    c, r = c1.w["center"], c1.w["radius"]
+    # Ritz values that are converged on the oracle side are reproduced
+    good = ohsrr.in_disk(ref["lam"], c, r) & (ref["rho"] < 1e-8)
+    assert good.sum() >= 5
+    for l in ref["lam"][good]:
+        assert np.min(np.abs(lam - l)) / abs(l) < 1e-10
+    # residuals reported by the GPU are those of its own vectors
+    X = Xd.cpu().numpy()
+    e2, rho2 = ohsrr.residuals(c1.A, c1.B, lam, X, c, r, nA, nB)
+    fin = np.isfinite(lam)
+    assert np.allclose(rho[fin], rho2[fin], rtol=1e-6, atol=1e-16)
+    assert np.allclose(np.linalg.norm(X, axis=0), 1.0)
+
+
+# ---------------------------------------------------------------- a8: drivers
+@pytest.mark.parametrize("driver", [1, 2])
+def test_solve_c1_matches_dense_qz(ie, driver):
+    c = Case(ie, "c1_m24", driver=driver)
+    try:
+        k = c.w["k"]
+        Y0 = ie_inputs.orthonormal_random_block(c.n, k, seed=c.w["seed"])
+        Xd = dzeros(c.n, k)
+        st, lam, rho, e, nf, stats = ie.ie_solve(c.h, dblock(Y0), Xd, k)
+        assert st == ie.IE_OK, ie.ie_status_str(st)
+        ref = golden_eigs(c.w)
+        assert nf == len(ref) == 10
+        match_eigs(lam[:nf], ref)
+        assert np.all(rho[:nf] <= 1e-10)
+        X = Xd.cpu().numpy()[:, :nf]
+        e2, rho2 = ohsrr.residuals(c.A, c.B, lam[:nf], X, c.w["center"], c.w["radius"],
+                                   opencil.norm1(c.A), opencil.norm1(c.B))
+        assert np.all(rho2 <= 1e-10)
+        assert stats["converged"] == 1 and stats["n_found"] == nf
+    finally:
+        c.close()
+
+
+@pytest.mark.parametrize("name,driver", [("r1_m37", 1), ("r1_m37", 2), ("m1_m64", 2), ("m1_m64", 1)])
+def test_solve_matches_golden(ie, name, driver):
+    c = Case(ie, name, driver=driver)
+    try:
+        k = c.w["k"]
+        Y0 = ie_inputs.orthonormal_random_block(c.n, k, seed=c.w["seed"])
+        Xd = dzeros(c.n, k)
+        st, lam, rho, e, nf, stats = ie.ie_solve(c.h, dblock(Y0), Xd, k)
+        assert st == ie.IE_OK, ie.ie_status_str(st)
+        ref = golden_eigs(c.w)
+        assert nf == len(ref)
+        match_eigs(lam[:nf], ref)
+        assert np.all(rho[:nf] <= 1e-10)
+    finally:
+        c.close()
+
+
+def test_solve_with_seeded_random_start(ie):
+    c = Case(ie, "c1_m24")
+    try:
+        k = c.w["k"]
+        Xd = dzeros(c.n, k)
+        st, lam, rho, e, nf, stats = ie.ie_solve(c.h, None, Xd, k)
+        assert st == ie.IE_OK
+        match_eigs(lam[:nf], golden_eigs(c.w))
+    finally:
+        c.close()
+
+
+# ---------------------------------------------------------------- error paths
+def test_invalid_arguments(ie, c1):
+    w = c1.w
+    bad = ie.ie_opts_default(k=0)
+    st, h = ie.ie_create(c1.n, c1.pen.offsets, c1.Ad, c1.Bd, w["center"], w["radius"], 4, 4, bad)
+    assert st == ie.IE_ERR_ARG
+    st, h = ie.ie_create(c1.n, c1.pen.offsets, c1.Ad, c1.Bd, w["center"], -1.0, 4, 4)
+    assert st == ie.IE_ERR_ARG
+    st, h = ie.ie_create(c1.n, c1.pen.offsets, c1.Ad, c1.Bd, w["center"], 1.0, 0, 4)
+    assert st == ie.IE_ERR_ARG
+    Y = dzeros(c1.n, w["k"] + 1)
+    assert ie.ie_filter_apply(c1.h, Y, dzeros(c1.n, w["k"] + 1)) == ie.IE_ERR_ARG
+
+
+def test_singular_pencil_reports_zero_pivot(ie):
+    """A column of K = pB - A that is exactly zero for every pole (A and B share a zero
+    column) gives a zero pivot: IE_ERR_SINGULAR, reported on the host, no GPU fault."""
+    n = 64
+    offsets = np.array([-1, 0, 1], dtype=np.int64)
+    A = np.zeros((3, n), dtype=np.complex128)
+    B = np.zeros((3, n), dtype=np.complex128)
+    A[1] = np.arange(1, n + 1)
+    B[1] = 1.0
+    A[1, 17] = 0.0
+    B[1, 17] = 0.0
+    st, h = ie.ie_create(n, offsets, torch.from_numpy(A).to(DEV), torch.from_numpy(B).to(DEV),
+                         10.0, 2.5, 4, 4, ie.ie_opts_default(k=4))
+    assert st == ie.IE_ERR_SINGULAR
+    ie.ie_destroy(h)
