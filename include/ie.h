@@ -92,6 +92,11 @@ typedef struct {
   double t_filter_ms;      /* total filter time of the last ie_solve (or the last filter call) */
   double t_hsrr_ms;        /* total HSRR time of the last ie_solve */
   double max_rho_found;    /* max rho_i over the filtered pairs */
+  int64_t solve_launches;  /* band-solve kernel launches since create */
+  double t_solve_ms;       /* their summed device time (CUDA events on the launch stream) */
+  double solve_flops;      /* their algorithmic flops: q*k*(8 (n kl + n kv - band corners) + 12 n) */
+  double solve_bytes;      /* their algorithmic DRAM bytes (factors once per launch, RHS, y, x) */
+  int64_t kernel_launches; /* CUDA kernels launched by this library in this process so far */
 } ie_stats;
 
 /* ie_create: computes the inner poles/weights (Eq. pwtp, q points) and the outer

@@ -7,7 +7,13 @@
 #include <cooperative_groups.h>
 #include <cstdio>
 
+#include <atomic>
+
 #include "ie_internal.cuh"
+
+static std::atomic<int64_t> g_launches{0};
+void ie_count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+int64_t ie_launch_count() { return g_launches.load(std::memory_order_relaxed); }
 
 // ----------------------------------------------------------------------------------------------
 // SpMV: Y = (aA A + aB B) X on a block, DIA storage M[i, i+off_d] = dia[d*n + i].
@@ -34,7 +40,7 @@ void launch_spmv(const DiaDev& P, cplx aA, cplx aB, const cplx* X, int64_t ldx,
   if (k <= 0 || P.n <= 0) return;
   const int useA = (aA.x != 0.0 || aA.y != 0.0), useB = (aB.x != 0.0 || aB.y != 0.0);
   dim3 grid((unsigned)((P.n + 255) / 256), (unsigned)k);
-  spmv_dia_kernel<<<grid, 256, 0, s>>>(P, aA, aB, useA, useB, X, ldx, xoff, Y, ldy);
+  spmv_dia_kernel<<<grid, 256, 0, s>>>(P, aA, aB, useA, useB, X, ldx, xoff, Y, ldy); ie_count_launch();
 }
 
 // ----------------------------------------------------------------------------------------------
@@ -70,7 +76,7 @@ void launch_assemble(const DiaDev& P, const cplx* d_poles, int q, int kl, int ld
                      int64_t n_pad, cplx* AB, cudaStream_t s) {
   const int64_t tot = n_pad * ldab;
   dim3 grid((unsigned)((tot + 255) / 256), (unsigned)q);
-  assemble_kernel<<<grid, 256, 0, s>>>(P, d_poles, kl, ldab, n_pad, AB);
+  assemble_kernel<<<grid, 256, 0, s>>>(P, d_poles, kl, ldab, n_pad, AB); ie_count_launch();
 }
 
 // ----------------------------------------------------------------------------------------------
@@ -93,7 +99,7 @@ void launch_norm1_cols(const DiaDev& P, int which, double* d_out, double* /*scra
                        cudaStream_t s) {
   cudaMemsetAsync(d_out, 0, sizeof(double), s);
   norm1_kernel<<<(unsigned)((P.n + 255) / 256), 256, 0, s>>>(P, which,
-                                                               (unsigned long long*)d_out);
+                                                               (unsigned long long*)d_out); ie_count_launch();
 }
 
 // ----------------------------------------------------------------------------------------------
@@ -288,6 +294,7 @@ cudaError_t launch_band_lu(int q, int64_t n, int kl, int ldab, int64_t n_pad, cp
   if (ctas_per_pole) *ctas_per_pole = P;
   cudaMemsetAsync(bar, 0, sizeof(unsigned) * 2 * q, s);
   void* args[] = {&n, &kl, &ldab, &n_pad, &AB, &piv, &dinv, &bar, &status, &P, &nown_max};
+  ie_count_launch();
   return cudaLaunchCooperativeKernel((void*)band_lu_kernel, dim3(q * P), dim3(256), args, smem, s);
 }
 
@@ -615,7 +622,7 @@ static cudaError_t launch_solve_t(const SolveArgs& a, int q, int threads, size_t
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   dim3 grid((unsigned)((a.k + NC - 1) / NC), (unsigned)q);
-  band_solve_kernel<NC, SPT><<<grid, threads, smem, s>>>(a);
+  band_solve_kernel<NC, SPT><<<grid, threads, smem, s>>>(a); ie_count_launch();
   return cudaGetLastError();
 }
 
@@ -680,5 +687,5 @@ void launch_pole_sum(int q, int64_t n, int k, const cplx* Xp, int64_t ldx, int64
                      cplx* GV, int64_t ldg, cudaStream_t s) {
   if (k <= 0) return;
   dim3 grid((unsigned)((n + 255) / 256), (unsigned)k);
-  pole_sum_kernel<<<grid, 256, 0, s>>>(q, n, Xp, ldx, xstride, GV, ldg);
+  pole_sum_kernel<<<grid, 256, 0, s>>>(q, n, Xp, ldx, xstride, GV, ldg); ie_count_launch();
 }

@@ -114,6 +114,18 @@ struct ie_handle_s {
   std::vector<char> conv_h;
   ie_stats stats{};
   int64_t g_columns = 0;
+  // band-solve launch timing: event pairs pending until the next stream synchronisation
+  struct SolveRec { cudaEvent_t a, b; double flops, bytes; };
+  std::vector<SolveRec> pending;
+  std::vector<cudaEvent_t> event_pool;
+  int64_t solve_launches = 0;
+  double t_solve_ms = 0, solve_flops = 0, solve_bytes = 0;
+  cudaEvent_t get_event() {
+    if (!event_pool.empty()) { cudaEvent_t e = event_pool.back(); event_pool.pop_back(); return e; }
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    return e;
+  }
   uint32_t salt = 1;
   std::vector<void*> allocs;
 
@@ -133,9 +145,13 @@ struct ie_handle_s {
     cudaFree(p_);
   }
   ~ie_handle_s() {
+    for (auto& r : pending) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
+    for (auto e : event_pool) cudaEventDestroy(e);
     for (void* v : allocs) cudaFree(v);
   }
 };
+
+static void fill_solve_stats(ie_handle h, ie_stats* out);
 
 extern "C" void ie_opts_default(ie_opts* o) {
   if (!o) return;
@@ -395,9 +411,28 @@ static ie_status stage_out(ie_handle h, const cplx* src, int64_t lds, int k, ie_
                        cudaMemcpyDefault, s));
   return IE_OK;
 }
+// Accumulates the device time of band-solve launches whose events have completed
+// (called after a stream synchronisation).
+static void flush_solve_timing(ie_handle h) {
+  std::vector<ie_handle_s::SolveRec> keep;
+  for (auto& r : h->pending) {
+    if (cudaEventQuery(r.b) != cudaSuccess) { cudaGetLastError(); keep.push_back(r); continue; }
+    float ms = 0;
+    cudaEventElapsedTime(&ms, r.a, r.b);
+    h->t_solve_ms += ms;
+    h->solve_flops += r.flops;
+    h->solve_bytes += r.bytes;
+    h->solve_launches += 1;
+    h->event_pool.push_back(r.a);
+    h->event_pool.push_back(r.b);
+  }
+  h->pending.swap(keep);
+}
+
 static ie_status check_status(ie_handle h, cudaStream_t s) {
   CK(cudaGetLastError());
   CK(cudaStreamSynchronize(s));
+  flush_solve_timing(h);
   int st[ST_COUNT];
   CK(cudaMemcpy(st, h->status, sizeof(st), cudaMemcpyDeviceToHost));
   if (st[ST_TIMEOUT]) return IE_ERR_TIMEOUT;
@@ -410,8 +445,22 @@ static ie_status apply_G_dev(ie_handle h, const cplx* V, int64_t ldv, const int6
                              cplx* GV, int64_t ldg, cudaStream_t s) {
   if (k <= 0) return IE_OK;
   launch_spmv(h->P, make_double2(0, 0), make_double2(1, 0), V, ldv, d_off, k, h->BVw, h->n, s);
+  ie_handle_s::SolveRec rec;
+  rec.a = h->get_event();
+  rec.b = h->get_event();
+  {
+    // algorithmic work of one launch: forward n*kl and backward n*kv complex FMAs per (pole,
+    // column) less the band corners, plus two complex products per row (1/u_jj and w_i)
+    const double n = (double)h->n, kl = h->kl, kv = h->kv, q = h->q;
+    const double fwd = n * kl - 0.5 * kl * (kl + 1), bwd = n * kv - 0.5 * kv * (kv + 1);
+    rec.flops = q * k * (8.0 * (fwd + bwd) + 12.0 * n);
+    rec.bytes = q * n * (16.0 * (kl + kv + 1) + 4.0) + 16.0 * n * k * (1.0 + 3.0 * q);
+  }
+  cudaEventRecord(rec.a, s);
   CK(launch_band_solve(h->q, h->n, h->kl, h->ldab, h->n_pad, h->AB, h->piv, h->dinv, h->d_weights,
                        h->BVw, h->n, k, h->Xp, h->n, h->n * (int64_t)h->kmax, h->status, s));
+  cudaEventRecord(rec.b, s);
+  h->pending.push_back(rec);
   launch_pole_sum(h->q, h->n, k, h->Xp, h->n, h->n * (int64_t)h->kmax, GV, ldg, s);
   h->g_columns += k;
   return IE_OK;
@@ -483,6 +532,7 @@ static ie_status filter_dev(ie_handle h, const cplx* Y, int64_t ldy, int k, cplx
                   h->d_res, s);
     CK(cudaMemcpyAsync(res.data(), h->d_res, sizeof(double) * kact, cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
+    flush_solve_timing(h);
     for (int i = 0; i < kact; ++i) {
       const int c = act[i];
       h->jc_h[c] += 1;
@@ -758,7 +808,7 @@ extern "C" ie_status ie_solve(ie_handle h, const ie_complex* Y0_any, int64_t ldy
   }
   *n_found = nf;
   S.converged = converged ? 1 : 0;
-  S.g_columns = h->g_columns;
+  fill_solve_stats(h, &S);
   if (stats) *stats = S;
   (void)any_noconv;
   return converged ? IE_OK : IE_ERR_NOCONV;
@@ -801,9 +851,19 @@ extern "C" ie_status ie_get_factor(ie_handle h, int32_t pole, ie_complex* h_ab, 
   return IE_OK;
 }
 
+static void fill_solve_stats(ie_handle h, ie_stats* out) {
+  out->g_columns = h->g_columns;
+  out->solve_launches = h->solve_launches;
+  out->t_solve_ms = h->t_solve_ms;
+  out->solve_flops = h->solve_flops;
+  out->solve_bytes = h->solve_bytes;
+  out->kernel_launches = ie_launch_count();
+}
+
 extern "C" ie_status ie_get_stats(ie_handle h, ie_stats* out) {
   if (!h || !out) return IE_ERR_ARG;
+  flush_solve_timing(h);
   *out = h->stats;
-  out->g_columns = h->g_columns;
+  fill_solve_stats(h, out);
   return IE_OK;
 }

@@ -136,27 +136,27 @@ void launch_orth_cgs2(int64_t n, int k, cplx* Q, int64_t ldq, uint64_t seed, uin
   for (int j = 0; j < k; ++j) {
     cplx* x = Q + (int64_t)j * ldq;
     // pass 1 (its norm slot = ||x||^2 before projection)
-    odot_kernel<<<nchunk, 256, 0, s>>>(n, Q, ldq, j, x, part, LD, nullptr);
-    odot_reduce_kernel<<<1, 256, 0, s>>>(j, part, nchunk, LD, h1, nullptr);
-    copy_scalar_kernel<<<1, 1, 0, s>>>(h1 + j, nrm0);
-    if (j > 0) oupdate_kernel<<<nb, 256, 0, s>>>(n, Q, ldq, j, x, h1, nullptr);
+    odot_kernel<<<nchunk, 256, 0, s>>>(n, Q, ldq, j, x, part, LD, nullptr); ie_count_launch();
+    odot_reduce_kernel<<<1, 256, 0, s>>>(j, part, nchunk, LD, h1, nullptr); ie_count_launch();
+    copy_scalar_kernel<<<1, 1, 0, s>>>(h1 + j, nrm0); ie_count_launch();
+    if (j > 0) oupdate_kernel<<<nb, 256, 0, s>>>(n, Q, ldq, j, x, h1, nullptr); ie_count_launch();
     // pass 2
-    odot_kernel<<<nchunk, 256, 0, s>>>(n, Q, ldq, j, x, part, LD, nullptr);
-    odot_reduce_kernel<<<1, 256, 0, s>>>(j, part, nchunk, LD, h2, nullptr);
-    if (j > 0) oupdate_kernel<<<nb, 256, 0, s>>>(n, Q, ldq, j, x, h2, nullptr);
+    odot_kernel<<<nchunk, 256, 0, s>>>(n, Q, ldq, j, x, part, LD, nullptr); ie_count_launch();
+    odot_reduce_kernel<<<1, 256, 0, s>>>(j, part, nchunk, LD, h2, nullptr); ie_count_launch();
+    if (j > 0) oupdate_kernel<<<nb, 256, 0, s>>>(n, Q, ldq, j, x, h2, nullptr); ie_count_launch();
     // norm after the two passes
-    odot_kernel<<<nchunk, 256, 0, s>>>(n, Q, ldq, 0, x, part, LD, nullptr);
-    odot_reduce_kernel<<<1, 256, 0, s>>>(0, part, nchunk, LD, h3 + j, nullptr);
+    odot_kernel<<<nchunk, 256, 0, s>>>(n, Q, ldq, 0, x, part, LD, nullptr); ie_count_launch();
+    odot_reduce_kernel<<<1, 256, 0, s>>>(0, part, nchunk, LD, h3 + j, nullptr); ie_count_launch();
     // rank guard: replace by a seeded random vector, then project it twice (gated)
-    oguard_kernel<<<nb, 256, 0, s>>>(n, j, nrm0, h3, x, seed, salt, flags + j);
+    oguard_kernel<<<nb, 256, 0, s>>>(n, j, nrm0, h3, x, seed, salt, flags + j); ie_count_launch();
     for (int pass = 0; pass < 2; ++pass) {
-      odot_kernel<<<nchunk, 256, 0, s>>>(n, Q, ldq, j, x, part, LD, flags + j);
-      odot_reduce_kernel<<<1, 256, 0, s>>>(j, part, nchunk, LD, h1, flags + j);
-      if (j > 0) oupdate_kernel<<<nb, 256, 0, s>>>(n, Q, ldq, j, x, h1, flags + j);
+      odot_kernel<<<nchunk, 256, 0, s>>>(n, Q, ldq, j, x, part, LD, flags + j); ie_count_launch();
+      odot_reduce_kernel<<<1, 256, 0, s>>>(j, part, nchunk, LD, h1, flags + j); ie_count_launch();
+      if (j > 0) oupdate_kernel<<<nb, 256, 0, s>>>(n, Q, ldq, j, x, h1, flags + j); ie_count_launch();
     }
-    odot_kernel<<<nchunk, 256, 0, s>>>(n, Q, ldq, 0, x, part, LD, flags + j);
-    odot_reduce_kernel<<<1, 256, 0, s>>>(0, part, nchunk, LD, h3 + j, flags + j);
-    onormalize_kernel<<<nb, 256, 0, s>>>(n, j, h3, x);
+    odot_kernel<<<nchunk, 256, 0, s>>>(n, Q, ldq, 0, x, part, LD, flags + j); ie_count_launch();
+    odot_reduce_kernel<<<1, 256, 0, s>>>(0, part, nchunk, LD, h3 + j, flags + j); ie_count_launch();
+    onormalize_kernel<<<nb, 256, 0, s>>>(n, j, h3, x); ie_count_launch();
   }
 }
 
@@ -211,8 +211,8 @@ void launch_gram(int64_t n, int k, const cplx* W, int64_t ldw, const cplx* Y, in
                  cplx* C, cplx* scratch, cudaStream_t s) {
   const int nchunk = (int)((n + GCH - 1) / GCH);
   const int tiles = (k + 31) / 32;
-  gram_part_kernel<<<dim3(tiles, tiles, nchunk), 256, 0, s>>>(n, k, W, ldw, Y, ldy, scratch);
-  gram_reduce_kernel<<<(k * k + 255) / 256, 256, 0, s>>>(k, scratch, nchunk, C);
+  gram_part_kernel<<<dim3(tiles, tiles, nchunk), 256, 0, s>>>(n, k, W, ldw, Y, ldy, scratch); ie_count_launch();
+  gram_reduce_kernel<<<(k * k + 255) / 256, 256, 0, s>>>(k, scratch, nchunk, C); ie_count_launch();
 }
 
 // ---------------- complex QZ (one CTA) --------------------------------------------------------
@@ -483,7 +483,7 @@ cudaError_t launch_qz(int k, cplx* Ah, cplx* Bh, cplx* Z, cplx* alpha, cplx* bet
     if (e != cudaSuccess) return e;
   }
   qz_kernel<<<1, 256, use_smem ? smem : 0, s>>>(k, Ah, Bh, Z, alpha, beta, M, VR, status,
-                                                use_smem);
+                                                use_smem); ie_count_launch();
   return cudaGetLastError();
 }
 
@@ -508,7 +508,7 @@ __global__ void gemm_small_kernel(int64_t n, int k, const cplx* X, int64_t ldx, 
 }
 void launch_gemm_small(int64_t n, int k, const cplx* X, int64_t ldx, const cplx* M, cplx* Y,
                        int64_t ldy, cudaStream_t s) {
-  gemm_small_kernel<<<dim3((unsigned)((n + 255) / 256), k), 256, 0, s>>>(n, k, X, ldx, M, Y, ldy);
+  gemm_small_kernel<<<dim3((unsigned)((n + 255) / 256), k), 256, 0, s>>>(n, k, X, ldx, M, Y, ldy); ie_count_launch();
 }
 
 __global__ void scale_cols_kernel(int64_t n, cplx* X, int64_t ldx, const double* nrm) {
@@ -522,7 +522,7 @@ void launch_normalize_cols(int64_t n, int k, cplx* X, int64_t ldx, double* scrat
                            cudaStream_t s) {
   double* nrm = scratch;
   launch_colnorm2(n, k, X, ldx, nrm, scratch + k, s);
-  scale_cols_kernel<<<dim3((unsigned)((n + 255) / 256), k), 256, 0, s>>>(n, X, ldx, nrm);
+  scale_cols_kernel<<<dim3((unsigned)((n + 255) / 256), k), 256, 0, s>>>(n, X, ldx, nrm); ie_count_launch();
 }
 
 __global__ void resid_part_kernel(DiaDev P, const cplx* X, int64_t ldx, const cplx* lam,
@@ -568,8 +568,8 @@ __global__ void resid_reduce_kernel(int k, const double* part, int nblk, double*
 void launch_residual_norms(const DiaDev& P, int k, const cplx* X, int64_t ldx, const cplx* lam,
                            double* d_out, double* scratch, cudaStream_t s) {
   const int nblk = (int)((P.n + 255) / 256);
-  resid_part_kernel<<<dim3(nblk, k), 256, 0, s>>>(P, X, ldx, lam, scratch, nblk);
-  resid_reduce_kernel<<<(3 * k + 127) / 128, 128, 0, s>>>(k, scratch, nblk, d_out);
+  resid_part_kernel<<<dim3(nblk, k), 256, 0, s>>>(P, X, ldx, lam, scratch, nblk); ie_count_launch();
+  resid_reduce_kernel<<<(3 * k + 127) / 128, 128, 0, s>>>(k, scratch, nblk, d_out); ie_count_launch();
 }
 
 __global__ void permute_cols_kernel(int64_t n, const cplx* X, int64_t ldx, const int* perm,
@@ -581,7 +581,7 @@ __global__ void permute_cols_kernel(int64_t n, const cplx* X, int64_t ldx, const
 void launch_permute_cols(int64_t n, int k, const cplx* X, int64_t ldx, const int* perm, cplx* Y,
                          int64_t ldy, cudaStream_t s) {
   permute_cols_kernel<<<dim3((unsigned)((n + 255) / 256), k), 256, 0, s>>>(n, X, ldx, perm, Y,
-                                                                           ldy);
+                                                                           ldy); ie_count_launch();
 }
 
 __global__ void random_block_kernel(int64_t n, cplx* X, int64_t ldx, uint64_t seed,
@@ -592,7 +592,7 @@ __global__ void random_block_kernel(int64_t n, cplx* X, int64_t ldx, uint64_t se
 }
 void launch_random_block(int64_t n, int k, cplx* X, int64_t ldx, uint64_t seed, uint32_t salt,
                          cudaStream_t s) {
-  random_block_kernel<<<dim3((unsigned)((n + 255) / 256), k), 256, 0, s>>>(n, X, ldx, seed, salt);
+  random_block_kernel<<<dim3((unsigned)((n + 255) / 256), k), 256, 0, s>>>(n, X, ldx, seed, salt); ie_count_launch();
 }
 
 __global__ void copy_cols_kernel(int64_t n, const cplx* X, int64_t ldx, cplx* Y, int64_t ldy) {
@@ -603,5 +603,5 @@ __global__ void copy_cols_kernel(int64_t n, const cplx* X, int64_t ldx, cplx* Y,
 void launch_copy_cols(int64_t n, int k, const cplx* X, int64_t ldx, cplx* Y, int64_t ldy,
                       cudaStream_t s) {
   if (k <= 0) return;
-  copy_cols_kernel<<<dim3((unsigned)((n + 255) / 256), k), 256, 0, s>>>(n, X, ldx, Y, ldy);
+  copy_cols_kernel<<<dim3((unsigned)((n + 255) / 256), k), 256, 0, s>>>(n, X, ldx, Y, ldy); ie_count_launch();
 }

@@ -66,6 +66,10 @@ __device__ __forceinline__ unsigned long long ie_globaltimer() {
   return t;
 }
 
+// Process-wide count of kernel launches issued by this library (exposed in ie_stats).
+void ie_count_launch();
+int64_t ie_launch_count();
+
 // ---------------- kernel launchers (defined in ie_band.cu / ie_krylov.cu / ie_hsrr.cu) -------
 struct DiaDev {
   int64_t n;

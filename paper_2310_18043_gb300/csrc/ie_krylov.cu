@@ -54,8 +54,8 @@ void launch_colnorm2(int64_t n, int k, const cplx* X, int64_t ldx, double* d_out
                      double* d_scratch, cudaStream_t s) {
   if (k <= 0) return;
   const int nchunk = colnorm_chunks(n);
-  colnorm2_part_kernel<<<dim3(nchunk, k), 256, 0, s>>>(n, X, ldx, d_scratch, nchunk);
-  sum_parts_sqrt_kernel<<<(k + 127) / 128, 128, 0, s>>>(k, d_scratch, nchunk, d_out);
+  colnorm2_part_kernel<<<dim3(nchunk, k), 256, 0, s>>>(n, X, ldx, d_scratch, nchunk); ie_count_launch();
+  sum_parts_sqrt_kernel<<<(k + 127) / 128, 128, 0, s>>>(k, d_scratch, nchunk, d_out); ie_count_launch();
 }
 
 // ---------------- Krylov start: beta_c = ||ytilde_c||, v_0 = ytilde_c / beta_c -----------------
@@ -75,7 +75,7 @@ __global__ void krylov_start_kernel(KrylovDev K, const cplx* Yt, int64_t ldy) {
 void launch_krylov_start(const KrylovDev& K, int k, const cplx* Yt, int64_t ldy, double* scratch,
                          cudaStream_t s) {
   launch_colnorm2(K.n, k, Yt, ldy, K.beta, scratch, s);
-  krylov_start_kernel<<<dim3((unsigned)((K.n + 255) / 256), k), 256, 0, s>>>(K, Yt, ldy);
+  krylov_start_kernel<<<dim3((unsigned)((K.n + 255) / 256), k), 256, 0, s>>>(K, Yt, ldy); ie_count_launch();
 }
 
 __global__ void active_offsets_kernel(KrylovDev K, const int* act, int kact, int64_t* off) {
@@ -87,7 +87,7 @@ __global__ void active_offsets_kernel(KrylovDev K, const int* act, int kact, int
 void launch_active_offsets(const KrylovDev& K, const int* act, int kact, int64_t* d_off,
                            cudaStream_t s) {
   if (kact <= 0) return;
-  active_offsets_kernel<<<(kact + 127) / 128, 128, 0, s>>>(K, act, kact, d_off);
+  active_offsets_kernel<<<(kact + 127) / 128, 128, 0, s>>>(K, act, kact, d_off); ie_count_launch();
 }
 
 // ---------------- CGS2 Arnoldi step ---------------------------------------------------------
@@ -239,15 +239,15 @@ void launch_arnoldi_cgs2(const KrylovDev& K, const int* act, int kact, cplx* W, 
   double* part2 = scratch + 2 * (int64_t)kact * nchunk * LD; // kact*nblk doubles
   const dim3 gdot(nchunk, kact), gupd(nblk, kact);
   // pass 1: h1 = V^H w (+ ||w||^2), w -= V h1
-  mdot_kernel<<<gdot, 256, 0, s>>>(K, act, W, ldw, part, nchunk, LD, 1);
-  mdot_reduce_kernel<<<kact, 128, 0, s>>>(K, act, part, nchunk, LD, h1, 1);
-  mupdate_kernel<<<gupd, 256, 0, s>>>(K, act, W, ldw, h1, LD, nullptr, nblk);
+  mdot_kernel<<<gdot, 256, 0, s>>>(K, act, W, ldw, part, nchunk, LD, 1); ie_count_launch();
+  mdot_reduce_kernel<<<kact, 128, 0, s>>>(K, act, part, nchunk, LD, h1, 1); ie_count_launch();
+  mupdate_kernel<<<gupd, 256, 0, s>>>(K, act, W, ldw, h1, LD, nullptr, nblk); ie_count_launch();
   // pass 2: h2 = V^H w, w -= V h2, ||w||^2
-  mdot_kernel<<<gdot, 256, 0, s>>>(K, act, W, ldw, part, nchunk, LD, 0);
-  mdot_reduce_kernel<<<kact, 128, 0, s>>>(K, act, part, nchunk, LD, h2, 0);
-  mupdate_kernel<<<gupd, 256, 0, s>>>(K, act, W, ldw, h2, LD, part2, nblk);
-  arnoldi_finish_kernel<<<kact, 256, 0, s>>>(K, act, kact, h1, h2, LD, part2, nblk, scale);
-  arnoldi_normalize_kernel<<<gupd, 256, 0, s>>>(K, act, W, ldw, scale);
+  mdot_kernel<<<gdot, 256, 0, s>>>(K, act, W, ldw, part, nchunk, LD, 0); ie_count_launch();
+  mdot_reduce_kernel<<<kact, 128, 0, s>>>(K, act, part, nchunk, LD, h2, 0); ie_count_launch();
+  mupdate_kernel<<<gupd, 256, 0, s>>>(K, act, W, ldw, h2, LD, part2, nblk); ie_count_launch();
+  arnoldi_finish_kernel<<<kact, 256, 0, s>>>(K, act, kact, h1, h2, LD, part2, nblk, scale); ie_count_launch();
+  arnoldi_normalize_kernel<<<gupd, 256, 0, s>>>(K, act, W, ldw, scale); ie_count_launch();
 }
 
 // ---------------- multi-shift Givens ---------------------------------------------------------
@@ -324,7 +324,7 @@ void launch_givens(const KrylovDev& K, const int* act, int kact, const cplx* d_s
   const int tot = kact * nshift;
   givens_kernel<<<(tot + 127) / 128, 128, 0, s>>>(K, act, kact, d_shifts, nshift, (double*)rot_c,
                                                   rot_s, gvec, from_zero,
-                                                  (unsigned long long*)d_res);
+                                                  (unsigned long long*)d_res); ie_count_launch();
 }
 
 // ---------------- combine: U_c = V_c z_c, z_c = -sum_l wt_l y_l (+ odd beta e_1) -------------
@@ -419,7 +419,7 @@ void launch_krylov_combine(const KrylovDev& K, int k, const cplx* d_shifts, cons
   const int tot = k * nshift;
   if (nshift > 0)
     ls_solve_kernel<<<(tot + 63) / 64, 64, 0, s>>>(K, k, d_shifts, nshift, (double*)rot_c, rot_s,
-                                                  Rscratch, y);
-  zcombine_kernel<<<k, 128, 0, s>>>(K, k, d_wts, nshift, odd, y, z);
-  vz_kernel<<<dim3((unsigned)((K.n + 255) / 256), k), 256, 0, s>>>(K, z, U, ldu);
+                                                  Rscratch, y); ie_count_launch();
+  zcombine_kernel<<<k, 128, 0, s>>>(K, k, d_wts, nshift, odd, y, z); ie_count_launch();
+  vz_kernel<<<dim3((unsigned)((K.n + 255) / 256), k), 256, 0, s>>>(K, z, U, ldu); ie_count_launch();
 }

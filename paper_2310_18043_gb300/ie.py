@@ -43,7 +43,9 @@ class ie_stats(C.Structure):
                 ("gmres_iters_max", C.c_int32), ("gmres_iters_min", C.c_int32),
                 ("converged", C.c_int32), ("g_columns", C.c_int64), ("t_factor_ms", C.c_double),
                 ("t_filter_ms", C.c_double), ("t_hsrr_ms", C.c_double),
-                ("max_rho_found", C.c_double)]
+                ("max_rho_found", C.c_double), ("solve_launches", C.c_int64),
+                ("t_solve_ms", C.c_double), ("solve_flops", C.c_double),
+                ("solve_bytes", C.c_double), ("kernel_launches", C.c_int64)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}

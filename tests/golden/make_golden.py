@@ -5,7 +5,7 @@ Arnoldi otherwise, as the paper's reference eigenvalues come from eigs, Sec. 6.2
 
 Disk recipe: centre = the median eigenvalue (sort by real part, ties by imaginary
 part, index floor(n/2)); radius = midpoint of the N-th and (N+1)-th distances from
-the centre, so the disk holds exactly N eigenvalues. For n > 4096 the median is not
+the centre, so the disk holds exactly N eigenvalues. For n > 1600 the median is not
 computed exactly: the centre is the eigenvalue nearest the point
 (4/h^2)/1.025 + i*mean(gamma) -- the median of the unperturbed operator scaled by
 the mean of B's diagonal (checked against the exact median at small m by this script).
@@ -62,12 +62,21 @@ def build(name, spec):
         c0 = proxy_center(pen)
         near0 = ref.nearest_eigenvalues(A, B, c0, 8)
         c = near0[0]
-        near = ref.nearest_eigenvalues(A, B, c, n_in + 12)
+        # Shift-invert from two shifts that are not eigenvalues (c itself is one): the
+        # proxy point c0 and c offset by a quarter of the distance to c's nearest neighbour.
+        # Both runs must agree on every eigenvalue near c.
+        gap = float(np.sort(np.abs(near0 - c))[1])
+        runA = ref.nearest_eigenvalues(A, B, c0, n_in + 24)
+        runB = ref.nearest_eigenvalues(A, B, c + 0.25 * gap * np.exp(1j * np.pi / 3), n_in + 24)
+        near = runB[np.argsort(np.abs(runB - c))][: n_in + 8]
+        xerr = max(float(np.min(np.abs(runA - v)) / abs(v)) for v in near)
+        assert xerr < 1e-12, f"shift-invert runs disagree: {xerr}"
         d = np.abs(near - c)
         r = ref.disk_radius(d, n_in)
         inside = near[d < r]
         info["median_exact"] = False
         info["proxy_center"] = [c0.real, c0.imag]
+        info["crosscheck_rel"] = xerr
     inside = inside[np.argsort(np.abs(inside - c))]
     d_sorted = np.sort(np.abs(inside - c))
     out = dict(spec)

@@ -1,0 +1,84 @@
+"""Parity at the full bench size (m = 256, n = 65,536, q = p = 8, k = 64), in the launch
+configuration bench.py times: sampled outputs that the oracle can compute one column at
+a time (G and the filter on a few columns), and, for the drivers, the reference eigenvalues
+in tests/golden (shift-invert Arnoldi) plus the residual bound that holds at any size."""
+import numpy as np
+import pytest
+
+import ie_inputs
+from oracle import inner, msgmres, hsrr as ohsrr
+
+from test_gpu_parity import Case, dblock, dzeros, golden_eigs, match_eigs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ie():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2310_18043_gb300 import build as b
+    b.build()
+    import paper_2310_18043_gb300.ie as ie_
+    return ie_
+
+
+@pytest.fixture(scope="module")
+def c2(ie):
+    c = Case(ie, "c2_m256", m_max=150)
+    yield c
+    c.close()
+
+
+@pytest.fixture(scope="module")
+def oracle_G(c2):
+    return inner.InnerOperator(c2.A, c2.B, c2.w["center"], c2.w["radius"], c2.w["q"])
+
+
+def test_c2_apply_G_sampled_columns(ie, c2, oracle_G):
+    """Full 64-column launch; the oracle checks 3 sampled columns (first, middle, last)."""
+    k = 64
+    V = ie_inputs.random_block(c2.n, k, seed=21)
+    GVd = dzeros(c2.n, k)
+    assert ie.ie_apply_G(c2.h, dblock(V), GVd) == ie.IE_OK
+    got = GVd.cpu().numpy()
+    for col in (0, 31, 63):
+        ref = oracle_G.apply(V[:, col])
+        err = np.linalg.norm(got[:, col] - ref) / np.linalg.norm(ref)
+        assert err < 1e-11, (col, err)
+
+
+def test_c2_filter_sampled_column(ie, c2, oracle_G):
+    """Filter of the full bench block; the oracle filters one sampled column."""
+    k = 64
+    Y = ie_inputs.orthonormal_random_block(c2.n, k, seed=1)
+    Ud = dzeros(c2.n, k)
+    assert ie.ie_filter_apply(c2.h, dblock(Y), Ud) == ie.IE_OK
+    got = Ud.cpu().numpy()
+    ref = msgmres.filter_apply(oracle_G, Y[:, 17:18], c2.w["p"], tol=1e-12, m_max=150)
+    err = np.linalg.norm(got[:, 17] - ref[:, 0]) / np.linalg.norm(ref[:, 0])
+    assert err < 1e-9, err
+
+
+@pytest.mark.parametrize("driver", [1, 2])
+def test_c2_solve_matches_reference_eigenvalues(ie, driver):
+    c = Case(ie, "c2_m256", driver=driver, m_max=150)
+    try:
+        k = c.w["k"]
+        Y0 = ie_inputs.orthonormal_random_block(c.n, k, seed=c.w["seed"])
+        Xd = dzeros(c.n, k)
+        st, lam, rho, e, nf, stats = ie.ie_solve(c.h, dblock(Y0), Xd, k)
+        assert st == ie.IE_OK, ie.ie_status_str(st)
+        ref = golden_eigs(c.w)
+        assert nf == len(ref) == 40
+        match_eigs(lam[:nf], ref)
+        assert np.all(rho[:nf] <= 1e-10)
+        # the residual bound on the returned vectors, recomputed on the CPU
+        from oracle import pencil as opencil
+        X = Xd.cpu().numpy()[:, :nf]
+        _, rho2 = ohsrr.residuals(c.A, c.B, lam[:nf], X, c.w["center"], c.w["radius"],
+                                  opencil.norm1(c.A), opencil.norm1(c.B))
+        assert np.all(rho2 <= 1e-10)
+    finally:
+        c.close()

@@ -221,26 +221,31 @@ def test_filter_host_buffers_equal_device(ie, c1):
 
 # ---------------------------------------------------------------- a7: HSRR
 def test_hsrr_matches_oracle(ie, c1):
-    k = c1.w["k"]
-    Y = ie_inputs.orthonormal_random_block(c1.n, k, seed=6)
-    G = inner.InnerOperator(c1.A, c1.B, c1.w["center"], c1.w["radius"], c1.w["q"])
-    U = msgmres.filter_apply(G, Y, c1.w["p"], tol=1e-12, m_max=100)
+    """HSRR on the same U: the oracle's Alg. 1 converged Ritz vectors, filtered once more.
+    The Ritz values inside D (converged) agree to 1e-10; every finite Ritz value of the two
+    sides agrees loosely (same subspaces up to rounding)."""
+    from oracle import drivers
+    k, c, r = c1.w["k"], c1.w["center"], c1.w["radius"]
+    Y0 = ie_inputs.orthonormal_random_block(c1.n, k, seed=6)
+    sol = drivers.solve(c1.A, c1.B, c, r, c1.w["p"], c1.w["q"], Y0, driver=1)
+    G = inner.InnerOperator(c1.A, c1.B, c, r, c1.w["q"])
+    U = msgmres.filter_apply(G, sol["X"], c1.w["p"], tol=1e-12, m_max=100)
     Xd = dzeros(c1.n, k)
     st, lam, e, rho = ie.ie_hsrr(c1.h, dblock(U), Xd)
     assert st == ie.IE_OK
     nA, nB = opencil.norm1(c1.A), opencil.norm1(c1.B)
-    ref = ohsrr.hsrr(c1.A, c1.B, U, c1.w["center"], c1.w["center"], c1.w["radius"], nA, nB)
-    c, r = c1.w["center"], c1.w["radius"]
-    # Ritz values that are converged on the oracle side are reproduced
-    good = ohsrr.in_disk(ref["lam"], c, r) & (ref["rho"] < 1e-8)
-    assert good.sum() >= 5
-    for l in ref["lam"][good]:
-        assert np.min(np.abs(lam - l)) / abs(l) < 1e-10
-    # residuals reported by the GPU are those of its own vectors
+    ref = ohsrr.hsrr(c1.A, c1.B, U, c, c, r, nA, nB)
+    good = ohsrr.in_disk(ref["lam"], c, r) & (ref["rho"] < 1e-10)
+    assert good.sum() == 10
+    match_eigs(lam[ohsrr.in_disk(lam, c, r) & (rho < 1e-10)], ref["lam"][good])
+    fin = np.isfinite(ref["lam"])
+    for l in ref["lam"][fin]:
+        assert np.min(np.abs(lam - l)) / abs(l) < 1e-6
+    # the residuals the GPU reports are those of its own vectors
     X = Xd.cpu().numpy()
     e2, rho2 = ohsrr.residuals(c1.A, c1.B, lam, X, c, r, nA, nB)
-    fin = np.isfinite(lam)
-    assert np.allclose(rho[fin], rho2[fin], rtol=1e-6, atol=1e-16)
+    finite = np.isfinite(lam)
+    assert np.allclose(rho[finite], rho2[finite], rtol=1e-6, atol=1e-16)
     assert np.allclose(np.linalg.norm(X, axis=0), 1.0)
 
 
