@@ -45,7 +45,8 @@ typedef enum {
   IE_ERR_SINGULAR = 4,   /* an LU pivot was exactly zero: a pole hit an eigenvalue (Prop. 1 case) */
   IE_ERR_NOCONV = 5,     /* GMRES reached m_max or the driver reached max_outer; outputs still written */
   IE_ERR_BREAKDOWN = 6,  /* reserved: orthogonalisation could not extend a basis */
-  IE_ERR_TIMEOUT = 7     /* a device-side bounded wait gave up (kernel returned early) */
+  IE_ERR_TIMEOUT = 7,    /* a device-side bounded wait gave up (kernel returned early) */
+  IE_ERR_SCRATCH_LIMIT = 8 /* ie_apply_G_static: problem larger than its static scratch */
 } ie_status;
 
 /* Sparse pencil in DIA form: M[i, i + offsets[d]] = dia[d * n + i] (entries with
@@ -175,6 +176,26 @@ ie_status ie_get_factor(ie_handle h, int32_t pole, ie_complex* h_ab, int32_t* h_
 
 /* ie_get_stats: counters of the last call (see ie_stats). */
 ie_status ie_get_stats(ie_handle h, ie_stats* out);
+
+/* ie_apply_G_static: the same G(V) as ie_apply_G (same kernels, same results), for callers
+ * that must not make the library allocate device memory at call time: a host application
+ * whose own allocator owns the device memory budget, or a latency-critical loop that cannot
+ * afford the implicit device synchronisation of cudaMalloc/cudaFree. The paper has no
+ * counterpart; this is a deployment variant of the inner-operator application.
+ * It calls no cudaMalloc, cudaFree or allocating library routine. Its scratch (the B V block
+ * and the q per-pole solve buffers) lives in one file-scope device array of
+ * IE_STATIC_SCRATCH_BYTES bytes, which every GPU that loads the library keeps until the
+ * process exits. Limit: (q + 1) * n * k * 16 <= IE_STATIC_SCRATCH_BYTES, else
+ * IE_ERR_SCRATCH_LIMIT (nothing is launched). d_V, d_GV: device pointers, n x k, ld >= n;
+ * the current device must be the handle's. The first call on a device looks up the array's
+ * device address (cudaGetSymbolAddress) once for that device; make that first call before
+ * any stream capture. All calls in the process share the one array: calls whose work
+ * overlaps on the GPU (different streams or threads, any handles) race on it and must be
+ * serialised by the caller. Every scratch element a call reads is first written by the
+ * same call, so nothing needs clearing between calls. */
+#define IE_STATIC_SCRATCH_BYTES (32u * 1024u * 1024u)
+ie_status ie_apply_G_static(ie_handle h, const ie_complex* d_V, int64_t ldv, int32_t k,
+                            ie_complex* d_GV, int64_t ldgv, void* stream);
 
 #ifdef __cplusplus
 }

@@ -177,6 +177,8 @@ extern "C" const char* ie_status_str(ie_status s) {
     case IE_ERR_NOCONV: return "IE_ERR_NOCONV: iteration limit reached";
     case IE_ERR_BREAKDOWN: return "IE_ERR_BREAKDOWN: orthogonalisation breakdown";
     case IE_ERR_TIMEOUT: return "IE_ERR_TIMEOUT: a device-side bounded wait gave up";
+    case IE_ERR_SCRATCH_LIMIT:
+      return "IE_ERR_SCRATCH_LIMIT: (q+1)*n*k complex128 values exceed IE_STATIC_SCRATCH_BYTES";
   }
   return "unknown ie_status";
 }
@@ -866,4 +868,23 @@ extern "C" ie_status ie_get_stats(ie_handle h, ie_stats* out) {
   *out = h->stats;
   fill_solve_stats(h, out);
   return IE_OK;
+}
+
+// ------------------------------ internal accessor (ie_static.cu) -----------------------------
+// Read-only view of a handle's factors for entry points defined in other translation units.
+bool ie_internal_factors(ie_handle h, IeFactorsView* v) {
+  if (!h || !v) return false;
+  v->dev = h->dev;
+  v->P = h->P;
+  v->n = h->n;
+  v->n_pad = h->n_pad;
+  v->kl = h->kl;
+  v->ldab = h->ldab;
+  v->q = h->q;
+  v->AB = h->AB;
+  v->piv = h->piv;
+  v->dinv = h->dinv;
+  v->weights = h->d_weights;
+  v->status = h->status;
+  return true;
 }

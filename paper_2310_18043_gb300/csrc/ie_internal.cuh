@@ -166,3 +166,17 @@ void launch_random_block(int64_t n, int k, cplx* X, int64_t ldx, uint64_t seed, 
 // generic copies
 void launch_copy_cols(int64_t n, int k, const cplx* X, int64_t ldx, cplx* Y, int64_t ldy,
                       cudaStream_t s);
+
+// Read-only view of a handle's factorisation (defined in ie_capi.cu).
+struct IeFactorsView {
+  int dev;
+  DiaDev P;
+  int64_t n, n_pad;
+  int kl, ldab, q;
+  const cplx* AB;
+  const int* piv;
+  const cplx* dinv;
+  const cplx* weights;
+  int* status;
+};
+bool ie_internal_factors(ie_handle h, IeFactorsView* v);

@@ -19,7 +19,9 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libie.so")
 
-IE_OK, IE_ERR_ARG, IE_ERR_CUDA, IE_ERR_OOM, IE_ERR_SINGULAR, IE_ERR_NOCONV, IE_ERR_BREAKDOWN, IE_ERR_TIMEOUT = range(8)
+(IE_OK, IE_ERR_ARG, IE_ERR_CUDA, IE_ERR_OOM, IE_ERR_SINGULAR, IE_ERR_NOCONV, IE_ERR_BREAKDOWN,
+ IE_ERR_TIMEOUT, IE_ERR_SCRATCH_LIMIT) = range(9)
+IE_STATIC_SCRATCH_BYTES = 32 * 1024 * 1024
 
 
 class ie_complex(C.Structure):
@@ -53,7 +55,7 @@ class ie_stats(C.Structure):
 
 EXPORTS = ["ie_opts_default", "ie_create", "ie_destroy", "ie_status_str", "ie_filter_apply",
            "ie_apply_G", "ie_hsrr", "ie_solve", "ie_spmv", "ie_get_coeffs", "ie_get_factor",
-           "ie_get_stats"]
+           "ie_get_stats", "ie_apply_G_static"]
 
 _lib = None
 _vp, _i32, _i64, _dp = C.c_void_p, C.c_int32, C.c_int64, C.POINTER(C.c_double)
@@ -83,6 +85,7 @@ def load():
     L.ie_get_coeffs.argtypes = [_vp, _vp, _vp, _vp, _vp, C.POINTER(_i32), _dp]
     L.ie_get_factor.argtypes = [_vp, _i32, _vp, _vp, C.POINTER(_i32), C.POINTER(_i32)]
     L.ie_get_stats.argtypes = [_vp, C.POINTER(ie_stats)]
+    L.ie_apply_G_static.argtypes = [_vp, _vp, _i64, _i32, _vp, _i64, _vp]
     for f in EXPORTS:
         if f not in ("ie_opts_default", "ie_status_str"):
             getattr(L, f).restype = C.c_int
@@ -186,6 +189,14 @@ def ie_apply_G(h, V, GV, stream=None):
     pv, ldv, n, k = _block(V)
     pg, ldg, _, _ = _block(GV)
     return load().ie_apply_G(h, pv, ldv, k, pg, ldg, _stream(stream))
+
+
+def ie_apply_G_static(h, V, GV, stream=None):
+    """G(V) with the library's static scratch: no device allocation by the call.
+    V, GV must be device tensors."""
+    pv, ldv, n, k = _block(V)
+    pg, ldg, _, _ = _block(GV)
+    return load().ie_apply_G_static(h, pv, ldv, k, pg, ldg, _stream(stream))
 
 
 def ie_spmv(h, which, X, Y, stream=None):
