@@ -34,6 +34,8 @@ SPECS = {
     "r1_m37": dict(m=37, seed=1, p=5, q=3, k=11, n_in=7, driver=1),
     # medium: n=4096, several column groups per pole
     "m1_m64": dict(m=64, seed=2, p=4, q=6, k=24, n_in=16, driver=2),
+    # profiling size: band 160, factors 1.6 GB (> L2, a few GB on the device)
+    "p1_m160": dict(m=160, seed=3, p=8, q=8, k=64, n_in=30, driver=1),
     # at scale: m=256 (n=65,536, band 256), q=p=8, k=64, ~40 eigenvalues, both drivers
     "c2_m256": dict(m=256, seed=0, p=8, q=8, k=64, n_in=40, driver=1),
 }
