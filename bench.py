@@ -30,7 +30,8 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 WORKLOAD = "c2_m256"
-FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12   # 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12     # 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # 152 SMs x 128 FP32 FMA/clk x 2 flop x 2.07 GHz
 
 
 def parse():
@@ -42,6 +43,9 @@ def parse():
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--precision", type=int, default=0, choices=[0, 1],
+                    help="0: complex128 factors and solves; 1: complex64 factors, FP32 solves, "
+                         "FP64 refinement")
     return ap.parse_args()
 
 
@@ -152,7 +156,7 @@ def run_native(args):
     stream = torch.cuda.current_stream()
     A_d = torch.from_numpy(pen.A_dia).to(device)
     B_d = torch.from_numpy(pen.B_dia).to(device)
-    opts = ie.ie_opts_default(k=k, m_max=150)
+    opts = ie.ie_opts_default(k=k, m_max=150, precision=args.precision)
     t0 = time.perf_counter()
     st, h = ie.ie_create(n, pen.offsets, A_d, B_d, w["center"], w["radius"], p, q, opts, stream)
     if st != ie.IE_OK:
@@ -194,10 +198,16 @@ def run_native(args):
     t_ms = ev0.elapsed_time(ev1)
     _, sB = ie.ie_get_stats(h)
     t_ms = max_over_ranks(t_ms, dist, device)
-    launches = sB["solve_launches"] - sA["solve_launches"]
-    solve_ms = sB["t_solve_ms"] - sA["t_solve_ms"]
-    solve_fl = sB["solve_flops"] - sA["solve_flops"]
-    solve_by = sB["solve_bytes"] - sA["solve_bytes"]
+    if args.precision == 0:
+        launches = sB["solve_launches"] - sA["solve_launches"]
+        solve_ms = sB["t_solve_ms"] - sA["t_solve_ms"]
+        solve_fl = sB["solve_flops"] - sA["solve_flops"]
+        solve_by = sB["solve_bytes"] - sA["solve_bytes"]
+    else:
+        launches = sB["solve32_launches"] - sA["solve32_launches"]
+        solve_ms = sB["t_solve32_ms"] - sA["t_solve32_ms"]
+        solve_fl = sB["solve32_flops"] - sA["solve32_flops"]
+        solve_by = None
     cols = k * args.steps * world
     value = cols / (t_ms / 1e3)
     gpu_launches = int(sB["kernel_launches"] - sA["kernel_launches"])   # counted by libie
@@ -227,11 +237,14 @@ def run_native(args):
     if rank == 0:
         inside = np.abs(last["lam"] - w["center"]) < w["radius"]
         achieved = solve_fl / (solve_ms / 1e3) / 1e12 if solve_ms > 0 else None
+        peak = FP64_PEAK_TFLOPS if args.precision == 0 else FP32_PEAK_TFLOPS
         line = {
             "metric": "filtered columns/sec (one Alg. 1 outer iteration: composite filter + HSRR)",
             "value": value, "unit": "filtered columns/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "c128", "data": "synthetic",
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "c128" if args.precision == 0 else "c64 solves + f64 refinement",
+            "data": "synthetic",
             "config": {"workload": f"{args.workload}: m={w['m']} convection-diffusion pencil, "
                                    f"n={n}, band {pen.half_bw}, q={q}, p={p}, k={k}, "
                                    f"disk with {len(w['eig_in_disk_re'])} eigenvalues",
@@ -241,13 +254,18 @@ def run_native(args):
                        "gmres_iters_max": last["gmres"],
                        "ritz_in_disk": int(inside.sum()),
                        "ritz_in_disk_rho_max": float(np.max(last["rho"][inside])) if inside.any() else None},
-            "roofline": {"bound": "alu", "kernel": "band_solve_kernel (FP64 complex band solves)",
-                         "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                         "frac": achieved / FP64_PEAK_TFLOPS if achieved else None,
-                         "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz "
-                                        "(measured FP64 FMA probe: 1.20 TFLOP/s)",
+            "roofline": {"bound": "alu",
+                         "kernel": "band_solve_kernel (%s complex band solves)"
+                                   % ("FP64" if args.precision == 0 else "FP32"),
+                         "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                         "frac": achieved / peak if achieved else None,
+                         "peak_source": ("derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz "
+                                         "(measured FP64 FMA probe: 1.20 TFLOP/s)")
+                                        if args.precision == 0 else
+                                        ("derived: 152 SMs x 128 FP32 FMA/clk x 2 flop x 2.07 GHz "
+                                         "(measured FP32 FMA probe: 70.2 TFLOP/s)"),
                          "traffic": None,
-                         "algorithmic_bytes_per_launch": solve_by / launches if launches else None,
+                         "algorithmic_bytes_per_launch": solve_by / launches if (launches and solve_by) else None,
                          "algorithmic_flops_per_launch": solve_fl / launches if launches else None,
                          "launches": launches, "avg_launch_ms": solve_ms / launches if launches else None,
                          "share_of_step": solve_ms / t_ms if t_ms > 0 else None},

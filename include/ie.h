@@ -74,10 +74,15 @@ typedef struct {
   int32_t sigma_is_center;/* 1: HSRR shift sigma = center (Sec. 6 preamble); 0: use sigma_re/im */
   double sigma_re, sigma_im;
   uint64_t seed;          /* seeds rank-guard replacement vectors and the random Y0 */
+  int32_t precision;      /* 0: complex128 band LU and solves. 1: mixed precision -- the
+                             factors are kept in complex64 (rounded from the complex128
+                             factorisation), the triangular solves run in FP32, and each
+                             K_i^{-1} b is refined in FP64: x += K~_i^{-1} (b - K_i x) */
+  int32_t refine_steps;   /* FP64 refinement steps per solve when precision = 1 (default 2) */
 } ie_opts;
 
 /* Fills defaults: k=16, driver=1, m_max=100, max_outer=10, tau_g=1e-2, tau=1e-10,
- * gmres_tol=1e-12, sigma = center, seed = 0. */
+ * gmres_tol=1e-12, sigma = center, seed = 0, precision = 0, refine_steps = 2. */
 void ie_opts_default(ie_opts* opts);
 
 /* Counters and timings of the last ie_solve / ie_filter_apply on a handle. */
@@ -98,6 +103,9 @@ typedef struct {
   double solve_flops;      /* their algorithmic flops: q*k*(8 (n kl + n kv - band corners) + 12 n) */
   double solve_bytes;      /* their algorithmic DRAM bytes (factors once per launch, RHS, y, x) */
   int64_t kernel_launches; /* CUDA kernels launched by this library in this process so far */
+  int64_t solve32_launches;/* complex64 band-solve launches (precision = 1) since create */
+  double t_solve32_ms;     /* their summed device time */
+  double solve32_flops;    /* their algorithmic flops (same count as solve_flops, in FP32) */
 } ie_stats;
 
 /* ie_create: computes the inner poles/weights (Eq. pwtp, q points) and the outer

@@ -15,7 +15,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libie.so")
-SOURCES = ["ie_band.cu", "ie_krylov.cu", "ie_hsrr.cu", "ie_capi.cu", "ie_static.cu"]
+SOURCES = ["ie_band.cu", "ie_solve.cu", "ie_krylov.cu", "ie_hsrr.cu", "ie_capi.cu", "ie_static.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]
 

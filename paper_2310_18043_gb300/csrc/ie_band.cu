@@ -1,9 +1,8 @@
 // Band kernels of the inner operator G (Sec. 3.2, Eq. linearsolve2):
 //   assembly of K_i = p_i B - A (Alg. 1 line 3) into LAPACK band storage,
 //   batched band LU with partial pivoting over all q poles in one cooperative launch,
-//   forward (P, L) + backward (U) band solves on n x k blocks with the factor panels
-//   staged into shared memory by bulk asynchronous copies (TMA, cp.async.bulk),
-//   the DIA SpMV with A and B, and the weighted pole sum.
+//   the DIA SpMV with A and B, the pole sums, and the complex64 factor copy and FP64
+//   residuals of the mixed-precision path (the triangular solves are in ie_solve.cu).
 #include <cooperative_groups.h>
 #include <cstdio>
 
@@ -299,380 +298,6 @@ cudaError_t launch_band_lu(int q, int64_t n, int kl, int ldab, int64_t n_pad, cp
 }
 
 // ----------------------------------------------------------------------------------------------
-// Band solves. One CTA per (pole, group of NC right-hand-side columns); the row recurrence is
-// sequential in n, so parallelism comes from poles x column groups and from the band width
-// inside each step. The active window of the recurrence lives in registers, one row slot per
-// thread (slot = row mod S): forward S = kl+1 rows j..j+kl, backward S = kv+1 rows j-kv..j.
-// Per step: the pivot/diagonal values are broadcast through a double-buffered shared cell,
-// every slot does NC complex FMAs with one factor entry, one __syncthreads.
-// Factor columns are staged NB at a time into an NSTAGE-deep shared ring by cp.async.bulk
-// (L parts for the forward sweep, U parts for the backward sweep), completion tracked by
-// mbarriers; all waits are bounded.
-
-namespace {
-constexpr int SOLVE_NB = 4;   // factor columns per staged panel (multiple of 4: 16-byte int copies)
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
-}
-__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
-               : "memory");
-}
-__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes,
-                                         uint32_t bar) {
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-          dst),
-      "l"(src), "r"(bytes), "r"(bar)
-      : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(ok)
-      : "r"(bar), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-// bounded wait: false after IE_WAIT_NS
-__device__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity) {
-  if (mbar_try_wait(bar, parity)) return true;
-  const unsigned long long t0 = ie_globaltimer();
-  while (true) {
-    for (int i = 0; i < 64; ++i)
-      if (mbar_try_wait(bar, parity)) return true;
-    if (ie_globaltimer() - t0 > IE_WAIT_NS) return false;
-  }
-}
-}  // namespace
-
-struct SolveArgs {
-  int64_t n, n_pad, ldab, ldr, ldx, xstride;
-  int kl, kv, k, nstage;
-  const cplx* AB;
-  const int* piv;
-  const cplx* dinv;
-  const cplx* weights;
-  const cplx* RHS;
-  cplx* X;
-  int* status;
-};
-
-template <int NC, int SPT>
-__global__ void __launch_bounds__(640, 1) band_solve_kernel(SolveArgs a) {
-  const int pole = blockIdx.y;
-  const int c0 = blockIdx.x * NC;
-  const int ncol = min(NC, a.k - c0);
-  const int T = blockDim.x, tid = threadIdx.x;
-  const int kl = a.kl, kv = a.kv;
-  const int64_t n = a.n;
-  const cplx* ABp = a.AB + (int64_t)pole * a.n_pad * a.ldab;
-  const int* pivp = a.piv + (int64_t)pole * a.n_pad;
-  const cplx* dinvp = a.dinv + (int64_t)pole * a.n_pad;
-  cplx* Xo = a.X + (int64_t)pole * a.xstride;
-  const cplx* R = a.RHS;
-  const cplx w = a.weights[pole];
-
-  extern __shared__ __align__(128) unsigned char sm_raw[];
-  uint64_t* mbar = (uint64_t*)sm_raw;                      // nstage mbarriers
-  cplx* bc = (cplx*)(sm_raw + 128);                        // [2][2][NC] broadcast cells
-  unsigned char* stage0 = sm_raw + 128 + 4 * NC * sizeof(cplx) + 128;
-  stage0 = (unsigned char*)(((uintptr_t)stage0 + 127) & ~(uintptr_t)127);
-  const int NB = SOLVE_NB;
-  const size_t fwd_cols_bytes = (size_t)NB * kl * sizeof(cplx);
-  const size_t bwd_cols_bytes = (size_t)NB * kv * sizeof(cplx);
-  const size_t stage_bytes = ((bwd_cols_bytes + NB * sizeof(cplx)) + 127) & ~(size_t)127;
-  __shared__ int s_fail;
-
-  if (tid == 0) {
-    s_fail = 0;
-    for (int i = 0; i < a.nstage; ++i) mbar_init(smem_u32(&mbar[i]), 1);
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-  }
-  __syncthreads();
-
-  const int64_t npanel = a.n_pad / NB;
-  // ------------------------------- forward: P L y = rhs -------------------------------------
-  auto issue_fwd = [&](int64_t P, int st) {
-    unsigned char* dst = stage0 + (size_t)st * stage_bytes;
-    const uint32_t bar = smem_u32(&mbar[st]);
-    const uint32_t bytes = (uint32_t)(fwd_cols_bytes + NB * sizeof(int));
-    mbar_expect_tx(bar, bytes);
-    for (int jj = 0; jj < NB; ++jj) {
-      const int64_t col = P * NB + jj;
-      bulk_g2s(smem_u32(dst + (size_t)jj * kl * sizeof(cplx)), ABp + col * a.ldab + kv + 1,
-               (uint32_t)(kl * sizeof(cplx)), bar);
-    }
-    bulk_g2s(smem_u32(dst + fwd_cols_bytes), pivp + P * NB, (uint32_t)(NB * sizeof(int)), bar);
-  };
-  const int S = kl + 1;
-  cplx v[SPT][NC], nxt[SPT][NC];
-  int off[SPT];
-  if (tid == 0)
-    for (int st = 0; st < a.nstage && st < npanel; ++st) issue_fwd(st, st);
-  {
-    const int p0 = __ldg(pivp);
-#pragma unroll
-    for (int u = 0; u < SPT; ++u) {
-      const int s = tid + u * T;
-      off[u] = s;
-      const int64_t r = s;
-#pragma unroll
-      for (int c = 0; c < NC; ++c) {
-        v[u][c] = (s < S && r < n && c < ncol) ? R[(int64_t)(c0 + c) * a.ldr + r] : cmk(0, 0);
-        nxt[u][c] = (s < S && r + S < n && c < ncol) ? R[(int64_t)(c0 + c) * a.ldr + r + S]
-                                                     : cmk(0, 0);
-      }
-      if (s < S) {
-        if (r == p0)
-#pragma unroll
-          for (int c = 0; c < NC; ++c) bc[0 * 2 * NC + 0 * NC + c] = v[u][c];
-        if (r == 0)
-#pragma unroll
-          for (int c = 0; c < NC; ++c) bc[0 * 2 * NC + 1 * NC + c] = v[u][c];
-      }
-    }
-  }
-  __syncthreads();
-  bool failed = false;
-  for (int64_t P = 0; P < npanel && !failed; ++P) {
-    const int st = (int)(P % a.nstage);
-    if (!mbar_wait_bounded(smem_u32(&mbar[st]), (uint32_t)((P / a.nstage) & 1))) s_fail = 1;
-    __syncthreads();
-    if (s_fail) { failed = true; break; }
-    const cplx* Lst = (const cplx*)(stage0 + (size_t)st * stage_bytes);
-    const int* pst = (const int*)(stage0 + (size_t)st * stage_bytes + fwd_cols_bytes);
-    for (int jj = 0; jj < NB; ++jj) {
-      const int64_t j = P * NB + jj;
-      if (j >= n) break;
-      const int par = (int)(j & 1);
-      cplx x[NC], xj[NC];
-#pragma unroll
-      for (int c = 0; c < NC; ++c) {
-        x[c] = bc[par * 2 * NC + c];
-        xj[c] = bc[par * 2 * NC + NC + c];
-      }
-      const int64_t jp = pst[jj];
-      const int64_t jp1 = (j + 1 < n) ? ((jj + 1 < NB) ? pst[jj + 1] : __ldg(pivp + j + 1)) : -1;
-      const cplx* Lc = Lst + (size_t)jj * kl;
-#pragma unroll
-      for (int u = 0; u < SPT; ++u) {
-        const int s = tid + u * T;
-        if (s >= S) continue;
-        const int o = off[u];
-        int64_t rnew;
-        if (o == 0) {
-          // row j leaves: y_j = x; slot refilled with row j + S
-#pragma unroll
-          for (int c = 0; c < NC; ++c)
-            if (c < ncol) Xo[(int64_t)(c0 + c) * a.ldx + j] = x[c];
-          rnew = j + S;
-#pragma unroll
-          for (int c = 0; c < NC; ++c) {
-            v[u][c] = nxt[u][c];
-            nxt[u][c] = (rnew + S < n && c < ncol) ? R[(int64_t)(c0 + c) * a.ldr + rnew + S]
-                                                   : cmk(0, 0);
-          }
-          off[u] = S - 1;
-        } else {
-          const int64_t r = j + o;
-          const cplx l = Lc[o - 1];
-#pragma unroll
-          for (int c = 0; c < NC; ++c) {
-            cplx t = (r == jp) ? xj[c] : v[u][c];
-            v[u][c] = cfms(l, x[c], t);
-          }
-          off[u] = o - 1;
-          rnew = r;
-        }
-        const int npar = par ^ 1;
-        if (rnew == jp1)
-#pragma unroll
-          for (int c = 0; c < NC; ++c) bc[npar * 2 * NC + c] = v[u][c];
-        if (rnew == j + 1)
-#pragma unroll
-          for (int c = 0; c < NC; ++c) bc[npar * 2 * NC + NC + c] = v[u][c];
-      }
-      __syncthreads();
-    }
-    if (tid == 0 && P + a.nstage < npanel) issue_fwd(P + a.nstage, st);
-  }
-  if (failed) {
-    if (tid == 0) atomicExch(a.status + ST_TIMEOUT, 1);
-    // wait (bounded) for the copies that may still be in flight, then leave
-    for (int st = 0; st < a.nstage; ++st)
-      for (int ph = 0; ph < 2; ++ph) mbar_wait_bounded(smem_u32(&mbar[st]), (uint32_t)ph);
-    return;
-  }
-  __syncthreads();
-  // re-initialise the barriers for the backward sweep (every forward stage has completed)
-  if (tid == 0) {
-    for (int i = 0; i < a.nstage; ++i) {
-      asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_u32(&mbar[i])) : "memory");
-      mbar_init(smem_u32(&mbar[i]), 1);
-    }
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-  }
-  __syncthreads();
-  // ------------------------------- backward: U x = y ----------------------------------------
-  // panel B covers columns [n_pad - (B+1) NB, n_pad - B NB)
-  auto issue_bwd = [&](int64_t Bp, int st) {
-    unsigned char* dst = stage0 + (size_t)st * stage_bytes;
-    const uint32_t bar = smem_u32(&mbar[st]);
-    const int64_t cb0 = a.n_pad - (Bp + 1) * NB;
-    const uint32_t bytes = (uint32_t)(bwd_cols_bytes + NB * sizeof(cplx));
-    mbar_expect_tx(bar, bytes);
-    for (int jj = 0; jj < NB; ++jj)
-      bulk_g2s(smem_u32(dst + (size_t)jj * kv * sizeof(cplx)), ABp + (cb0 + jj) * a.ldab,
-               (uint32_t)(kv * sizeof(cplx)), bar);
-    bulk_g2s(smem_u32(dst + bwd_cols_bytes), dinvp + cb0, (uint32_t)(NB * sizeof(cplx)), bar);
-  };
-  const int Sb = kv + 1;
-  if (tid == 0)
-    for (int st = 0; st < a.nstage && st < npanel; ++st) issue_bwd(st, st);
-  {
-#pragma unroll
-    for (int u = 0; u < SPT; ++u) {
-      const int s = tid + u * T;
-      int o = (int)(((n - 1 - s) % Sb + Sb) % Sb);
-      off[u] = o;
-      const int64_t r = n - 1 - o;
-#pragma unroll
-      for (int c = 0; c < NC; ++c) {
-        v[u][c] = (s < Sb && r >= 0 && c < ncol) ? Xo[(int64_t)(c0 + c) * a.ldx + r] : cmk(0, 0);
-        nxt[u][c] = (s < Sb && r - Sb >= 0 && c < ncol) ? Xo[(int64_t)(c0 + c) * a.ldx + r - Sb]
-                                                        : cmk(0, 0);
-      }
-      if (s < Sb && r == n - 1) {
-        const int par = (int)((n - 1) & 1);
-#pragma unroll
-        for (int c = 0; c < NC; ++c) bc[par * 2 * NC + c] = v[u][c];
-      }
-    }
-  }
-  __syncthreads();
-  for (int64_t Bp = 0; Bp < npanel && !failed; ++Bp) {
-    const int st = (int)(Bp % a.nstage);
-    if (!mbar_wait_bounded(smem_u32(&mbar[st]), (uint32_t)((Bp / a.nstage) & 1))) s_fail = 1;
-    __syncthreads();
-    if (s_fail) { failed = true; break; }
-    const cplx* Ust = (const cplx*)(stage0 + (size_t)st * stage_bytes);
-    const cplx* dst_ = (const cplx*)(stage0 + (size_t)st * stage_bytes + bwd_cols_bytes);
-    const int64_t cb0 = a.n_pad - (Bp + 1) * NB;
-    for (int jj = NB - 1; jj >= 0; --jj) {
-      const int64_t j = cb0 + jj;
-      if (j >= n) continue;
-      const int par = (int)(j & 1);
-      const cplx dj = dst_[jj];
-      cplx xj[NC];
-#pragma unroll
-      for (int c = 0; c < NC; ++c) xj[c] = cmul(bc[par * 2 * NC + c], dj);
-      const cplx* Uc = Ust + (size_t)jj * kv;
-#pragma unroll
-      for (int u = 0; u < SPT; ++u) {
-        const int s = tid + u * T;
-        if (s >= Sb) continue;
-        const int o = off[u];
-        int64_t rnew;
-        if (o == 0) {
-#pragma unroll
-          for (int c = 0; c < NC; ++c)
-            if (c < ncol) Xo[(int64_t)(c0 + c) * a.ldx + j] = cmul(w, xj[c]);
-          rnew = j - Sb;
-#pragma unroll
-          for (int c = 0; c < NC; ++c) {
-            v[u][c] = nxt[u][c];
-            nxt[u][c] = (rnew - Sb >= 0 && c < ncol) ? Xo[(int64_t)(c0 + c) * a.ldx + rnew - Sb]
-                                                     : cmk(0, 0);
-          }
-          off[u] = kv;
-        } else {
-          const cplx uu = Uc[kv - o];
-#pragma unroll
-          for (int c = 0; c < NC; ++c) v[u][c] = cfms(uu, xj[c], v[u][c]);
-          off[u] = o - 1;
-          rnew = j - o;
-        }
-        if (rnew == j - 1) {
-          const int npar = par ^ 1;
-#pragma unroll
-          for (int c = 0; c < NC; ++c) bc[npar * 2 * NC + c] = v[u][c];
-        }
-      }
-      __syncthreads();
-    }
-    if (tid == 0 && Bp + a.nstage < npanel) issue_bwd(Bp + a.nstage, st);
-  }
-  if (failed) {
-    if (tid == 0) atomicExch(a.status + ST_TIMEOUT, 1);
-    for (int st = 0; st < a.nstage; ++st)
-      for (int ph = 0; ph < 2; ++ph) mbar_wait_bounded(smem_u32(&mbar[st]), (uint32_t)ph);
-  }
-}
-
-template <int NC, int SPT>
-static cudaError_t launch_solve_t(const SolveArgs& a, int q, int threads, size_t smem,
-                                  cudaStream_t s) {
-  cudaError_t e = cudaFuncSetAttribute(band_solve_kernel<NC, SPT>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  dim3 grid((unsigned)((a.k + NC - 1) / NC), (unsigned)q);
-  band_solve_kernel<NC, SPT><<<grid, threads, smem, s>>>(a); ie_count_launch();
-  return cudaGetLastError();
-}
-
-cudaError_t launch_band_solve(int q, int64_t n, int kl, int ldab, int64_t n_pad, const cplx* AB,
-                              const int* piv, const cplx* dinv, const cplx* d_weights,
-                              const cplx* RHS, int64_t ldr, int k, cplx* Xp, int64_t ldx,
-                              int64_t xstride, int* status, cudaStream_t s) {
-  if (k <= 0) return cudaSuccess;
-  int dev = 0, sms = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  SolveArgs a;
-  a.n = n; a.n_pad = n_pad; a.ldab = ldab; a.ldr = ldr; a.ldx = ldx; a.xstride = xstride;
-  a.kl = kl; a.kv = 2 * kl; a.k = k;
-  a.AB = AB; a.piv = piv; a.dinv = dinv; a.weights = d_weights; a.RHS = RHS; a.X = Xp;
-  a.status = status;
-  const int slots = a.kv + 1;
-  const int spt = slots > 640 ? 2 : 1;
-  if (slots > 1280) return cudaErrorInvalidValue;   // half bandwidth up to 639
-  int threads = ((slots + spt - 1) / spt + 31) / 32 * 32;
-  const size_t stage_bytes =
-      (((size_t)SOLVE_NB * a.kv * sizeof(cplx) + SOLVE_NB * sizeof(cplx)) + 127) & ~(size_t)127;
-  const size_t fixed = 128 + 4 * 4 * sizeof(cplx) + 128 + 128;
-  const size_t budget = 200 * 1024;
-  int nstage = (int)((budget - fixed) / stage_bytes);
-  if (nstage > 6) nstage = 6;
-  if (nstage < 2) return cudaErrorInvalidValue;
-  a.nstage = nstage;
-  const size_t smem = fixed + (size_t)nstage * stage_bytes;
-  // columns per CTA: the smallest NC that keeps q * ceil(k/NC) CTAs within one wave
-  int NC = 4;
-  for (int c = 1; c <= 4; ++c)
-    if ((int64_t)q * ((k + c - 1) / c) <= sms) { NC = c; break; }
-  if (spt == 1) {
-    switch (NC) {
-      case 1: return launch_solve_t<1, 1>(a, q, threads, smem, s);
-      case 2: return launch_solve_t<2, 1>(a, q, threads, smem, s);
-      case 3: return launch_solve_t<3, 1>(a, q, threads, smem, s);
-      default: return launch_solve_t<4, 1>(a, q, threads, smem, s);
-    }
-  } else {
-    switch (NC) {
-      case 1: return launch_solve_t<1, 2>(a, q, threads, smem, s);
-      case 2: return launch_solve_t<2, 2>(a, q, threads, smem, s);
-      default: return launch_solve_t<4, 2>(a, q, threads, smem, s);
-    }
-  }
-}
-
-// ----------------------------------------------------------------------------------------------
 __global__ void pole_sum_kernel(int q, int64_t n, const cplx* Xp, int64_t ldx, int64_t xstride,
                                 cplx* GV, int64_t ldg) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -688,4 +313,99 @@ void launch_pole_sum(int q, int64_t n, int k, const cplx* Xp, int64_t ldx, int64
   if (k <= 0) return;
   dim3 grid((unsigned)((n + 255) / 256), (unsigned)k);
   pole_sum_kernel<<<grid, 256, 0, s>>>(q, n, Xp, ldx, xstride, GV, ldg); ie_count_launch();
+}
+
+// GV[:, c] = sum_i w_i Xp[i][:, c]
+__global__ void pole_wsum_kernel(int q, int64_t n, const cplx* Xp, int64_t ldx, int64_t xstride,
+                                 const cplx* w, cplx* GV, int64_t ldg) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int c = blockIdx.y;
+  if (i >= n) return;
+  cplx acc = cmk(0, 0);
+  for (int p = 0; p < q; ++p) acc = cfma(w[p], Xp[(int64_t)p * xstride + (int64_t)c * ldx + i], acc);
+  GV[(int64_t)c * ldg + i] = acc;
+}
+
+void launch_pole_wsum(int q, int64_t n, int k, const cplx* Xp, int64_t ldx, int64_t xstride,
+                      const cplx* w, cplx* GV, int64_t ldg, cudaStream_t s) {
+  if (k <= 0) return;
+  dim3 grid((unsigned)((n + 255) / 256), (unsigned)k);
+  pole_wsum_kernel<<<grid, 256, 0, s>>>(q, n, Xp, ldx, xstride, w, GV, ldg); ie_count_launch();
+}
+
+// ----------------------------------------------------------------------------------------------
+// Mixed precision: complex64 copy of the factors in a layout whose column segments start on
+// 16-byte boundaries and have even lengths (bulk-copy rules): L32 column j = the kl L
+// multipliers padded to klp (even), U32 column j = U(j-kv..j-1, j) (kv = 2 kl entries),
+// dinv32 = 1/u_jj. Rounded from the FP64 factorisation.
+__global__ void factors_to_c64_kernel(int64_t n_pad, int kl, int ldab, int klp, const cplx* AB,
+                                      const cplx* dinv, float2* L32, float2* U32, float2* dinv32) {
+  const int pole = blockIdx.y;
+  const int kv = 2 * kl;
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int per = klp + kv + 1;
+  if (idx >= n_pad * per) return;
+  const int64_t j = idx / per;
+  const int t = (int)(idx - j * per);
+  const cplx* col = AB + ((int64_t)pole * n_pad + j) * ldab;
+  if (t < klp) {
+    const cplx v = (t < kl) ? col[kv + 1 + t] : cmk(0, 0);
+    L32[((int64_t)pole * n_pad + j) * klp + t] = make_float2((float)v.x, (float)v.y);
+  } else if (t < klp + kv) {
+    const cplx v = col[t - klp];
+    U32[((int64_t)pole * n_pad + j) * kv + (t - klp)] = make_float2((float)v.x, (float)v.y);
+  } else {
+    const cplx v = dinv[(int64_t)pole * n_pad + j];
+    dinv32[(int64_t)pole * n_pad + j] = make_float2((float)v.x, (float)v.y);
+  }
+}
+
+void launch_factors_to_c64(int q, int64_t n_pad, int kl, int ldab, int klp, const cplx* AB,
+                           const cplx* dinv, float2* L32, float2* U32, float2* dinv32,
+                           cudaStream_t s) {
+  const int64_t tot = n_pad * (klp + 2 * kl + 1);
+  dim3 grid((unsigned)((tot + 255) / 256), (unsigned)q);
+  factors_to_c64_kernel<<<grid, 256, 0, s>>>(n_pad, kl, ldab, klp, AB, dinv, L32, U32, dinv32); ie_count_launch();
+}
+
+// R32[i][:, c] = (complex64) (BV[:, c] - K_i X[i][:, c]), K_i = p_i B - A, for all poles i:
+// the FP64 residual of the mixed-precision refinement.
+__global__ void pole_residual_kernel(DiaDev P, const cplx* poles, const cplx* BV, int64_t ldb,
+                                     const cplx* X, int64_t ldx, int64_t xstride, float2* R32,
+                                     int64_t ldr, int64_t rstride) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int c = blockIdx.y, pole = blockIdx.z;
+  if (i >= P.n) return;
+  const cplx p = poles[pole];
+  const cplx* x = X + (int64_t)pole * xstride + (int64_t)c * ldx;
+  cplx acc = BV[(int64_t)c * ldb + i];
+  for (int d = 0; d < P.ndiag; ++d) {
+    const int64_t j = i + P.off[d];
+    if (j < 0 || j >= P.n) continue;
+    const cplx kij = csub(cmul(p, P.B[(int64_t)d * P.n + i]), P.A[(int64_t)d * P.n + i]);
+    acc = cfms(kij, x[j], acc);
+  }
+  R32[(int64_t)pole * rstride + (int64_t)c * ldr + i] = make_float2((float)acc.x, (float)acc.y);
+}
+
+void launch_pole_residual(const DiaDev& P, const cplx* d_poles, int q, int k, const cplx* BV,
+                          int64_t ldb, const cplx* X, int64_t ldx, int64_t xstride, float2* R32,
+                          int64_t ldr, int64_t rstride, cudaStream_t s) {
+  if (k <= 0) return;
+  dim3 grid((unsigned)((P.n + 255) / 256), (unsigned)k, (unsigned)q);
+  pole_residual_kernel<<<grid, 256, 0, s>>>(P, d_poles, BV, ldb, X, ldx, xstride, R32, ldr, rstride); ie_count_launch();
+}
+
+__global__ void to_c64_kernel(int64_t n, const cplx* X, int64_t ldx, float2* Y, int64_t ldy) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int c = blockIdx.y;
+  if (i >= n) return;
+  const cplx v = X[(int64_t)c * ldx + i];
+  Y[(int64_t)c * ldy + i] = make_float2((float)v.x, (float)v.y);
+}
+
+void launch_to_c64(int64_t n, int k, const cplx* X, int64_t ldx, float2* Y, int64_t ldy,
+                   cudaStream_t s) {
+  if (k <= 0) return;
+  to_c64_kernel<<<dim3((unsigned)((n + 255) / 256), (unsigned)k), 256, 0, s>>>(n, X, ldx, Y, ldy); ie_count_launch();
 }

@@ -70,6 +70,14 @@ struct ie_handle_s {
   unsigned* bar = nullptr;
   int* status = nullptr;
   int lu_ctas = 0;
+  // mixed precision (opts.precision = 1): complex64 factors and FP32-solve scratch
+  int precision = 0, refine = 2, klp = 0;
+  float2* L32 = nullptr;   // q * n_pad * klp
+  float2* U32 = nullptr;   // q * n_pad * kv
+  float2* dinv32 = nullptr;
+  float2* Y32 = nullptr;   // q * n * kmax
+  float2* R32 = nullptr;   // q * n * kmax
+  float2* BV32 = nullptr;  // n * kmax
   // workspaces
   int kmax = 0, m_max = 0;
   cplx* Xp = nullptr;     // q * n * kmax
@@ -115,11 +123,11 @@ struct ie_handle_s {
   ie_stats stats{};
   int64_t g_columns = 0;
   // band-solve launch timing: event pairs pending until the next stream synchronisation
-  struct SolveRec { cudaEvent_t a, b; double flops, bytes; };
+  struct SolveRec { cudaEvent_t a, b; double flops, bytes; int fp32; };
   std::vector<SolveRec> pending;
   std::vector<cudaEvent_t> event_pool;
-  int64_t solve_launches = 0;
-  double t_solve_ms = 0, solve_flops = 0, solve_bytes = 0;
+  int64_t solve_launches = 0, solve32_launches = 0;
+  double t_solve_ms = 0, solve_flops = 0, solve_bytes = 0, t_solve32_ms = 0, solve32_flops = 0;
   cudaEvent_t get_event() {
     if (!event_pool.empty()) { cudaEvent_t e = event_pool.back(); event_pool.pop_back(); return e; }
     cudaEvent_t e;
@@ -165,6 +173,8 @@ extern "C" void ie_opts_default(ie_opts* o) {
   o->gmres_tol = 1e-12;
   o->sigma_is_center = 1;
   o->seed = 0;
+  o->precision = 0;
+  o->refine_steps = 2;
 }
 
 extern "C" const char* ie_status_str(ie_status s) {
@@ -292,18 +302,21 @@ extern "C" ie_status ie_create(const ie_pencil* pen, ie_complex center, double r
       opts.max_outer < 1 || (opts.driver != 1 && opts.driver != 2))
     return IE_ERR_ARG;
   if (!(opts.gmres_tol > 0) || !(opts.tau > 0) || !(opts.tau_g > 0)) return IE_ERR_ARG;
+  if ((opts.precision != 0 && opts.precision != 1) || opts.refine_steps < 0 ||
+      opts.refine_steps > 20)
+    return IE_ERR_ARG;
   int kl = 0;
   for (int d = 0; d < pen->ndiag; ++d) {
     const int64_t o = pen->h_offsets[d];
     if (o <= -pen->n || o >= pen->n) return IE_ERR_ARG;
     kl = (int)std::max<int64_t>(kl, o < 0 ? -o : o);
   }
-  if (kl < 1 || 2 * kl + 1 > 1280) return IE_ERR_ARG;   // band solve supports half bandwidth <= 639
+  if (kl < 1 || 2 * kl + 8 > 1152) return IE_ERR_ARG;   // band solve supports half bandwidth <= 572
   cudaStream_t s = (cudaStream_t)stream;
   ie_handle h = new ie_handle_s();
   cudaGetDevice(&h->dev);
   h->n = pen->n;
-  h->n_pad = (pen->n + 3) / 4 * 4;
+  h->n_pad = (pen->n + 7) / 8 * 8;   // whole 8-column factor panels
   h->kl = kl;
   h->kv = 2 * kl;
   h->ldab = 3 * kl + 1;
@@ -316,6 +329,9 @@ extern "C" ie_status ie_create(const ie_pencil* pen, ie_complex center, double r
   h->kmax = opts.k;
   h->m_max = opts.m_max;
   h->sigma = opts.sigma_is_center ? h->center : zc(opts.sigma_re, opts.sigma_im);
+  h->precision = opts.precision;
+  h->refine = opts.refine_steps;
+  h->klp = kl + (kl & 1);
   auto fail = [&](ie_status st) { delete h; return st; };
   const size_t dia_bytes = sizeof(cplx) * (size_t)pen->ndiag * (size_t)pen->n;
   if (h->alloc(&h->d_A, (size_t)pen->ndiag * pen->n) != cudaSuccess) return fail(IE_ERR_OOM);
@@ -383,6 +399,19 @@ extern "C" ie_status ie_create(const ie_pencil* pen, ie_complex center, double r
   if (st[ST_TIMEOUT]) return fail(IE_ERR_TIMEOUT);
   ie_status ws = alloc_workspace(h);
   if (ws != IE_OK) return fail(ws);
+  if (h->precision == 1) {
+    const size_t nk = (size_t)h->n * h->kmax;
+    if (h->alloc(&h->L32, (size_t)q * h->n_pad * h->klp) != cudaSuccess ||
+        h->alloc(&h->U32, (size_t)q * h->n_pad * h->kv) != cudaSuccess ||
+        h->alloc(&h->dinv32, (size_t)q * h->n_pad) != cudaSuccess ||
+        h->alloc(&h->Y32, (size_t)q * nk) != cudaSuccess ||
+        h->alloc(&h->R32, (size_t)q * nk) != cudaSuccess ||
+        h->alloc(&h->BV32, nk) != cudaSuccess)
+      return fail(IE_ERR_OOM);
+    launch_factors_to_c64(q, h->n_pad, kl, h->ldab, h->klp, h->AB, h->dinv, h->L32, h->U32,
+                          h->dinv32, s);
+    if (cudaStreamSynchronize(s) != cudaSuccess) return fail(IE_ERR_CUDA);
+  }
   if (cudaGetLastError() != cudaSuccess) return fail(IE_ERR_CUDA);
   *out = h;
   return st[ST_SINGULAR] ? IE_ERR_SINGULAR : IE_OK;
@@ -421,10 +450,16 @@ static void flush_solve_timing(ie_handle h) {
     if (cudaEventQuery(r.b) != cudaSuccess) { cudaGetLastError(); keep.push_back(r); continue; }
     float ms = 0;
     cudaEventElapsedTime(&ms, r.a, r.b);
-    h->t_solve_ms += ms;
-    h->solve_flops += r.flops;
-    h->solve_bytes += r.bytes;
-    h->solve_launches += 1;
+    if (r.fp32) {
+      h->t_solve32_ms += ms;
+      h->solve32_flops += r.flops;
+      h->solve32_launches += 1;
+    } else {
+      h->t_solve_ms += ms;
+      h->solve_flops += r.flops;
+      h->solve_bytes += r.bytes;
+      h->solve_launches += 1;
+    }
     h->event_pool.push_back(r.a);
     h->event_pool.push_back(r.b);
   }
@@ -443,10 +478,13 @@ static ie_status check_status(ie_handle h, cudaStream_t s) {
 
 // ------------------------------ inner operator G ----------------------------------------------
 // GV = sum_i w_i K_i^{-1} B V (Eq. linearsolve2). V columns at V + off[c] when d_off != null.
+static ie_status apply_G_mixed(ie_handle h, int k, cplx* GV, int64_t ldg, cudaStream_t s);
+
 static ie_status apply_G_dev(ie_handle h, const cplx* V, int64_t ldv, const int64_t* d_off, int k,
                              cplx* GV, int64_t ldg, cudaStream_t s) {
   if (k <= 0) return IE_OK;
   launch_spmv(h->P, make_double2(0, 0), make_double2(1, 0), V, ldv, d_off, k, h->BVw, h->n, s);
+  if (h->precision == 1) return apply_G_mixed(h, k, GV, ldg, s);
   ie_handle_s::SolveRec rec;
   rec.a = h->get_event();
   rec.b = h->get_event();
@@ -457,6 +495,7 @@ static ie_status apply_G_dev(ie_handle h, const cplx* V, int64_t ldv, const int6
     const double fwd = n * kl - 0.5 * kl * (kl + 1), bwd = n * kv - 0.5 * kv * (kv + 1);
     rec.flops = q * k * (8.0 * (fwd + bwd) + 12.0 * n);
     rec.bytes = q * n * (16.0 * (kl + kv + 1) + 4.0) + 16.0 * n * k * (1.0 + 3.0 * q);
+    rec.fp32 = 0;
   }
   cudaEventRecord(rec.a, s);
   CK(launch_band_solve(h->q, h->n, h->kl, h->ldab, h->n_pad, h->AB, h->piv, h->dinv, h->d_weights,
@@ -464,6 +503,37 @@ static ie_status apply_G_dev(ie_handle h, const cplx* V, int64_t ldv, const int6
   cudaEventRecord(rec.b, s);
   h->pending.push_back(rec);
   launch_pole_sum(h->q, h->n, k, h->Xp, h->n, h->n * (int64_t)h->kmax, GV, ldg, s);
+  h->g_columns += k;
+  return IE_OK;
+}
+
+// Mixed precision (opts.precision = 1), B V already in h->BVw: per pole i,
+//   x_i = K~_i^{-1} BV (complex64 factors, FP32 solve), then refine_steps times
+//   x_i += K~_i^{-1} (BV - K_i x_i) with the residual in FP64; GV = sum_i w_i x_i.
+static ie_status apply_G_mixed(ie_handle h, int k, cplx* GV, int64_t ldg, cudaStream_t s) {
+  const int64_t n = h->n, ps = n * (int64_t)h->kmax;
+  const double nn = (double)n, kl = h->kl, kv = h->kv, q = h->q;
+  const double fwd = nn * kl - 0.5 * kl * (kl + 1), bwd = nn * kv - 0.5 * kv * (kv + 1);
+  const double flops = q * k * (8.0 * (fwd + bwd) + 12.0 * nn);
+  launch_to_c64(n, k, h->BVw, n, h->BV32, n, s);
+  for (int it = 0; it <= h->refine; ++it) {
+    if (it > 0)
+      launch_pole_residual(h->P, h->d_poles, h->q, k, h->BVw, n, h->Xp, n, ps, h->R32, n, ps, s);
+    ie_handle_s::SolveRec rec;
+    rec.a = h->get_event();
+    rec.b = h->get_event();
+    rec.flops = flops;
+    rec.bytes = 0;
+    rec.fp32 = 1;
+    cudaEventRecord(rec.a, s);
+    CK(launch_band_solve32(h->q, n, h->kl, h->n_pad, h->L32, h->klp, h->U32, h->kv, h->piv,
+                           h->dinv32, h->d_weights, it == 0 ? h->BV32 : h->R32, n,
+                           it == 0 ? 0 : ps, k, h->Y32, n, ps, h->Xp, n, ps, it > 0 ? 1 : 0,
+                           h->status, s));
+    cudaEventRecord(rec.b, s);
+    h->pending.push_back(rec);
+  }
+  launch_pole_wsum(h->q, n, k, h->Xp, n, ps, h->d_weights, GV, ldg, s);
   h->g_columns += k;
   return IE_OK;
 }
@@ -860,6 +930,9 @@ static void fill_solve_stats(ie_handle h, ie_stats* out) {
   out->solve_flops = h->solve_flops;
   out->solve_bytes = h->solve_bytes;
   out->kernel_launches = ie_launch_count();
+  out->solve32_launches = h->solve32_launches;
+  out->t_solve32_ms = h->t_solve32_ms;
+  out->solve32_flops = h->solve32_flops;
 }
 
 extern "C" ie_status ie_get_stats(ie_handle h, ie_stats* out) {

@@ -96,6 +96,25 @@ cudaError_t launch_band_solve(int q, int64_t n, int kl, int ldab, int64_t n_pad,
                               const int* piv, const cplx* dinv, const cplx* d_weights,
                               const cplx* RHS, int64_t ldr, int k, cplx* Xp, int64_t ldx,
                               int64_t xstride, int* status, cudaStream_t s);
+// Mixed precision: complex64 band solves; X (FP64, per pole) = x (accumulate = 0) or += x.
+// RHS column c of pole i at RHS + i*rstride + c*ldr (rstride 0: shared right-hand side).
+cudaError_t launch_band_solve32(int q, int64_t n, int kl, int64_t n_pad, const float2* L32,
+                                int64_t ldl, const float2* U32, int64_t ldu, const int* piv,
+                                const float2* dinv32, const cplx* d_weights, const float2* RHS,
+                                int64_t ldr, int64_t rstride, int k, float2* Y32, int64_t ldy,
+                                int64_t ystride, cplx* X, int64_t ldx, int64_t xstride,
+                                int accumulate, int* status, cudaStream_t s);
+void launch_factors_to_c64(int q, int64_t n_pad, int kl, int ldab, int klp, const cplx* AB,
+                           const cplx* dinv, float2* L32, float2* U32, float2* dinv32,
+                           cudaStream_t s);
+void launch_pole_residual(const DiaDev& P, const cplx* d_poles, int q, int k, const cplx* BV,
+                          int64_t ldb, const cplx* X, int64_t ldx, int64_t xstride, float2* R32,
+                          int64_t ldr, int64_t rstride, cudaStream_t s);
+void launch_to_c64(int64_t n, int k, const cplx* X, int64_t ldx, float2* Y, int64_t ldy,
+                   cudaStream_t s);
+// GV[:, c] = sum_i w_i Xp[i][:, c]
+void launch_pole_wsum(int q, int64_t n, int k, const cplx* Xp, int64_t ldx, int64_t xstride,
+                      const cplx* w, cplx* GV, int64_t ldg, cudaStream_t s);
 // GV[:, c] = sum_i Xp[i][:, c]
 void launch_pole_sum(int q, int64_t n, int k, const cplx* Xp, int64_t ldx, int64_t xstride,
                      cplx* GV, int64_t ldg, cudaStream_t s);

@@ -1,0 +1,501 @@
+// Band triangular solves of the inner operator G (Sec. 3.2, Eq. linearsolve2):
+// x_i = K_i^{-1} rhs with K_i = P_i^T L_i U_i from the batched band LU, for all q poles and
+// k right-hand sides in one launch. Complex128 (the plain path) or complex64 factors with
+// FP32 arithmetic (the mixed-precision path, refined in FP64 by the caller).
+//
+// One CTA per (pole, group of NC right-hand sides): the row recurrence is sequential in n,
+// so parallelism comes from poles x column groups and from the band width inside each step.
+// Forward sweep (P, L; LAPACK zgbtrs order: swap, then eliminate): the window of S = kl+1 rows
+// j..j+kl lives in registers, one row slot per thread (slot = row mod S); per row the pivot
+// values are broadcast through a double-buffered shared cell, one barrier per row.
+// Backward sweep (U), blocked: one block = one staged panel of NB columns; the NB head rows
+// are solved by NC threads (a small triangular solve), then every slot applies the NB columns
+// at once; two barriers per NB rows.
+// Factor columns (L parts forward, U parts backward, with pivots / 1/u_jj) are staged NB at a
+// time into a shared ring by cp.async.bulk (TMA bulk copies) with mbarrier completion; every
+// wait is bounded.
+#include "ie_internal.cuh"
+
+namespace {
+constexpr int NB = 8;   // factor columns per staged panel = backward block
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes,
+                                         uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          dst),
+      "l"(src), "r"(bytes), "r"(bar)
+      : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// bounded wait: false after IE_WAIT_NS
+__device__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const unsigned long long t0 = ie_globaltimer();
+  while (true) {
+    for (int i = 0; i < 64; ++i)
+      if (mbar_try_wait(bar, parity)) return true;
+    if (ie_globaltimer() - t0 > IE_WAIT_NS) return false;
+  }
+}
+
+// complex64 arithmetic (complex128 versions live in ie_internal.cuh)
+__device__ __forceinline__ float2 cfms(float2 a, float2 b, float2 c) {
+  return make_float2(fmaf(-a.x, b.x, fmaf(a.y, b.y, c.x)), fmaf(-a.x, b.y, fmaf(-a.y, b.x, c.y)));
+}
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+__device__ __forceinline__ double2 shfl_c(double2 v, int src) {
+  return make_double2(__shfl_sync(0xffffffffu, v.x, src), __shfl_sync(0xffffffffu, v.y, src));
+}
+__device__ __forceinline__ float2 shfl_c(float2 v, int src) {
+  return make_float2(__shfl_sync(0xffffffffu, v.x, src), __shfl_sync(0xffffffffu, v.y, src));
+}
+__device__ __forceinline__ double2 to_d(double2 v) { return v; }
+__device__ __forceinline__ double2 to_d(float2 v) { return make_double2(v.x, v.y); }
+}  // namespace
+
+template <typename CT>
+struct SolveArgsT {
+  int64_t n, n_pad;
+  int kl, kv, klp, kvp, k, nstage, mode;
+  // factors: column col's L part (kl entries, padded to klp) at L + pole*lstride + col*ldl,
+  // U part (rows col-kv..col-1, padded to kvp) at U + pole*ustride + col*ldu
+  const CT* L;
+  const CT* U;
+  int64_t ldl, ldu, lstride, ustride;
+  const int* piv;     // 0-based, pole stride n_pad
+  const CT* dinv;     // 1/u_jj, pole stride n_pad
+  const cplx* weights;
+  const CT* RHS;      // column c at RHS + pole*rstride + c*ldr
+  int64_t ldr, rstride;
+  CT* Y;              // forward result, column c at Y + pole*ystride + c*ldy
+  int64_t ldy, ystride;
+  cplx* X;            // output (mode 0: X == Y, X = w*x; mode 1: X = x; mode 2: X += x)
+  int64_t ldx, xstride;
+  int* status;
+};
+
+// REGS: register budget. The register file is split over the SM's 4 sub-partitions (16K
+// registers each) and a block's warps are spread over them, so a block of W warps needs
+// ceil(W/4) * 32 * REGS <= 16384: 112 registers allow 16 warps, 96 allow 20.
+template <typename CT, int NC, int SPT, int REGS>
+__global__ void __maxnreg__(REGS) band_solve_kernel(SolveArgsT<CT> a) {
+  const int pole = blockIdx.y;
+  const int c0 = blockIdx.x * NC;
+  const int ncol = min(NC, a.k - c0);
+  const int T = blockDim.x, tid = threadIdx.x;
+  const int kl = a.kl, kv = a.kv, klp = a.klp, kvp = a.kvp;
+  const int64_t n = a.n;
+  const CT* Lp = a.L + (int64_t)pole * a.lstride;
+  const CT* Up = a.U + (int64_t)pole * a.ustride;
+  const int* pivp = a.piv + (int64_t)pole * a.n_pad;
+  const CT* dinvp = a.dinv + (int64_t)pole * a.n_pad;
+  const CT* R = a.RHS + (int64_t)pole * a.rstride;
+  CT* Yo = a.Y + (int64_t)pole * a.ystride;
+  cplx* Xo = a.X + (int64_t)pole * a.xstride;
+  const cplx w = a.weights[pole];
+  const CT zero{};
+
+  extern __shared__ __align__(128) unsigned char sm_raw[];
+  uint64_t* mbar = (uint64_t*)sm_raw;                          // nstage mbarriers
+  CT* bc = (CT*)(sm_raw + 128);                                // [2][2][NC] broadcast cells
+  CT* hd = bc + 4 * NC;                                        // [NB][NC] head values
+  CT* xs = hd + NB * NC;                                       // [NB][NC] solved head
+  CT* hv = xs + NB * NC;                                       // [2NB][NC] forward block set
+  unsigned char* stage0 = (unsigned char*)(((uintptr_t)(hv + 2 * NB * NC) + 127) & ~(uintptr_t)127);
+  const size_t fwd_cols_bytes = (size_t)NB * klp * sizeof(CT);
+  const size_t bwd_cols_bytes = (size_t)NB * kvp * sizeof(CT);
+  const size_t stage_bytes = ((bwd_cols_bytes + NB * sizeof(CT)) + 127) & ~(size_t)127;
+  __shared__ int s_fail;
+
+  if (tid == 0) {
+    s_fail = 0;
+    for (int i = 0; i < a.nstage; ++i) mbar_init(smem_u32(&mbar[i]), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+
+  const int64_t npanel = a.n_pad / NB;
+  // ------------------------------- forward: P L y = rhs -------------------------------------
+  auto issue_fwd = [&](int64_t P, int st) {
+    unsigned char* dst = stage0 + (size_t)st * stage_bytes;
+    const uint32_t bar = smem_u32(&mbar[st]);
+    mbar_expect_tx(bar, (uint32_t)(fwd_cols_bytes + NB * sizeof(int)));
+    for (int jj = 0; jj < NB; ++jj)
+      bulk_g2s(smem_u32(dst + (size_t)jj * klp * sizeof(CT)), Lp + (P * NB + jj) * a.ldl,
+               (uint32_t)(klp * sizeof(CT)), bar);
+    bulk_g2s(smem_u32(dst + fwd_cols_bytes), pivp + P * NB, (uint32_t)(NB * sizeof(int)), bar);
+  };
+  const int S = kl + 1;
+  CT v[SPT][NC], nxt[SPT][NC];
+  int off[SPT];
+  if (tid == 0)
+    for (int st = 0; st < a.nstage && st < npanel; ++st) issue_fwd(st, st);
+  {
+    const int p0 = __ldg(pivp);
+#pragma unroll
+    for (int u = 0; u < SPT; ++u) {
+      const int s = tid + u * T;
+      off[u] = s;
+      const int64_t r = s;
+#pragma unroll
+      for (int c = 0; c < NC; ++c) {
+        v[u][c] = (s < S && r < n && c < ncol) ? R[(int64_t)(c0 + c) * a.ldr + r] : zero;
+        nxt[u][c] = (s < S && r + S < n && c < ncol) ? R[(int64_t)(c0 + c) * a.ldr + r + S] : zero;
+      }
+      if (s < S) {
+        if (r == p0)
+#pragma unroll
+          for (int c = 0; c < NC; ++c) bc[c] = v[u][c];
+        if (r == 0)
+#pragma unroll
+          for (int c = 0; c < NC; ++c) bc[NC + c] = v[u][c];
+      }
+    }
+  }
+  __syncthreads();
+  bool failed = false;
+  for (int64_t P = 0; P < npanel && !failed; ++P) {
+    const int st = (int)(P % a.nstage);
+    const int pnext = (P + 1 < npanel) ? __ldg(pivp + (P + 1) * NB) : -1;   // prefetched
+    if (!mbar_wait_bounded(smem_u32(&mbar[st]), (uint32_t)((P / a.nstage) & 1))) s_fail = 1;
+    __syncthreads();
+    if (s_fail) { failed = true; break; }
+    const CT* Lst = (const CT*)(stage0 + (size_t)st * stage_bytes);
+    const int* pst = (const int*)(stage0 + (size_t)st * stage_bytes + fwd_cols_bytes);
+    for (int jj = 0; jj < NB; ++jj) {
+      const int64_t j = P * NB + jj;
+      if (j >= n) break;
+      const int par = (int)(j & 1);
+      CT x[NC], xj[NC];
+#pragma unroll
+      for (int c = 0; c < NC; ++c) {
+        x[c] = bc[par * 2 * NC + c];
+        xj[c] = bc[par * 2 * NC + NC + c];
+      }
+      const int64_t jp = pst[jj];
+      const int64_t jp1 = (j + 1 < n) ? ((jj + 1 < NB) ? pst[jj + 1] : pnext) : -1;
+      const CT* Lc = Lst + (size_t)jj * klp;
+#pragma unroll
+      for (int u = 0; u < SPT; ++u) {
+        const int s = tid + u * T;
+        if (s >= S) continue;
+        const int o = off[u];
+        int64_t rnew;
+        if (o == 0) {
+          // row j leaves: y_j = x; the slot is refilled with row j + S
+#pragma unroll
+          for (int c = 0; c < NC; ++c)
+            if (c < ncol) Yo[(int64_t)(c0 + c) * a.ldy + j] = x[c];
+          rnew = j + S;
+#pragma unroll
+          for (int c = 0; c < NC; ++c) {
+            v[u][c] = nxt[u][c];
+            nxt[u][c] = (rnew + S < n && c < ncol) ? R[(int64_t)(c0 + c) * a.ldr + rnew + S] : zero;
+          }
+          off[u] = S - 1;
+        } else {
+          const int64_t r = j + o;
+          const CT l = Lc[o - 1];
+#pragma unroll
+          for (int c = 0; c < NC; ++c) v[u][c] = cfms(l, x[c], (r == jp) ? xj[c] : v[u][c]);
+          off[u] = o - 1;
+          rnew = r;
+        }
+        const int npar = par ^ 1;
+        if (rnew == jp1)
+#pragma unroll
+          for (int c = 0; c < NC; ++c) bc[npar * 2 * NC + c] = v[u][c];
+        if (rnew == j + 1)
+#pragma unroll
+          for (int c = 0; c < NC; ++c) bc[npar * 2 * NC + NC + c] = v[u][c];
+      }
+      __syncthreads();
+    }
+    if (tid == 0 && P + a.nstage < npanel) issue_fwd(P + a.nstage, st);
+  }
+  if (failed) {
+    if (tid == 0) atomicExch(a.status + ST_TIMEOUT, 1);
+    for (int st = 0; st < a.nstage; ++st)
+      for (int ph = 0; ph < 2; ++ph) mbar_wait_bounded(smem_u32(&mbar[st]), (uint32_t)ph);
+    return;
+  }
+  __syncthreads();
+  // re-initialise the barriers for the backward sweep (every forward stage has completed)
+  if (tid == 0) {
+    for (int i = 0; i < a.nstage; ++i) {
+      asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_u32(&mbar[i])) : "memory");
+      mbar_init(smem_u32(&mbar[i]), 1);
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  // ------------------------------- backward: U x = y (blocked) -------------------------------
+  // Block = panel Bp, top row j0 = n_pad - 1 - Bp*NB; window of Sb = kv + NB rows
+  // j0-Sb+1..j0 (slot = row mod Sb). Rows >= n are virtual: zero values, zero factor
+  // columns, zero 1/u_jj.
+  auto issue_bwd = [&](int64_t Bp, int st) {
+    unsigned char* dst = stage0 + (size_t)st * stage_bytes;
+    const uint32_t bar = smem_u32(&mbar[st]);
+    const int64_t cb0 = a.n_pad - (Bp + 1) * NB;
+    mbar_expect_tx(bar, (uint32_t)(bwd_cols_bytes + NB * sizeof(CT)));
+    for (int jj = 0; jj < NB; ++jj)
+      bulk_g2s(smem_u32(dst + (size_t)jj * kvp * sizeof(CT)), Up + (cb0 + jj) * a.ldu,
+               (uint32_t)(kvp * sizeof(CT)), bar);
+    bulk_g2s(smem_u32(dst + bwd_cols_bytes), dinvp + cb0, (uint32_t)(NB * sizeof(CT)), bar);
+  };
+  const int Sb = kv + NB;
+  int64_t row[SPT];
+  if (tid == 0)
+    for (int st = 0; st < a.nstage && st < npanel; ++st) issue_bwd(st, st);
+  {
+    const int64_t j0 = a.n_pad - 1;
+#pragma unroll
+    for (int u = 0; u < SPT; ++u) {
+      const int s = tid + u * T;
+      const int64_t r = j0 - (((j0 - s) % Sb) + Sb) % Sb;
+      row[u] = r;
+#pragma unroll
+      for (int c = 0; c < NC; ++c) {
+        v[u][c] = (s < Sb && r >= 0 && r < n && c < ncol) ? Yo[(int64_t)(c0 + c) * a.ldy + r] : zero;
+        const int64_t rn = r - Sb;
+        nxt[u][c] = (s < Sb && rn >= 0 && rn < n && c < ncol) ? Yo[(int64_t)(c0 + c) * a.ldy + rn]
+                                                             : zero;
+      }
+      if (s < Sb && r > j0 - NB)
+#pragma unroll
+        for (int c = 0; c < NC; ++c) hd[(int)(j0 - r) * NC + c] = v[u][c];
+    }
+  }
+  for (int64_t Bp = 0; Bp < npanel && !failed; ++Bp) {
+    const int st = (int)(Bp % a.nstage);
+    if (!mbar_wait_bounded(smem_u32(&mbar[st]), (uint32_t)((Bp / a.nstage) & 1))) s_fail = 1;
+    __syncthreads();
+    if (s_fail) { failed = true; break; }
+    // the previous panel's stage is free: refill it
+    if (tid == 0 && Bp >= 1 && Bp - 1 + a.nstage < npanel)
+      issue_bwd(Bp - 1 + a.nstage, (int)((Bp - 1) % a.nstage));
+    const CT* Ust = (const CT*)(stage0 + (size_t)st * stage_bytes);
+    const CT* dst_ = (const CT*)(stage0 + (size_t)st * stage_bytes + bwd_cols_bytes);
+    const int64_t j0 = a.n_pad - 1 - Bp * NB;
+    // head rows j0 - t (t = 0..NB-1); matrix column j0 - s2 is stage column NB-1-s2
+    if (tid < NC) {
+      const int c = tid;
+      for (int t = 0; t < NB; ++t) {
+        CT acc = hd[t * NC + c];
+        for (int s2 = (t - kv > 0 ? t - kv : 0); s2 < t; ++s2)   // band: t - s2 <= kv
+          acc = cfms(Ust[(size_t)(NB - 1 - s2) * kvp + kv - (t - s2)], xs[s2 * NC + c], acc);
+        xs[t * NC + c] = cmul(acc, dst_[NB - 1 - t]);
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int u = 0; u < SPT; ++u) {
+      const int s = tid + u * T;
+      if (s >= Sb) continue;
+      int64_t r = row[u];
+      if (r > j0 - NB) {
+        const int t = (int)(j0 - r);
+        if (r < n) {
+#pragma unroll
+          for (int c = 0; c < NC; ++c) {
+            if (c >= ncol) continue;
+            const CT xv = xs[t * NC + c];
+            if constexpr (sizeof(CT) == sizeof(cplx)) {
+              if (a.mode == 0) {
+                Yo[(int64_t)(c0 + c) * a.ldy + r] = cmul(w, xv);
+                continue;
+              }
+            }
+            if (a.mode == 1) {
+              Xo[(int64_t)(c0 + c) * a.ldx + r] = to_d(xv);
+            } else {
+              cplx* p = Xo + (int64_t)(c0 + c) * a.ldx + r;
+              *p = cadd(*p, to_d(xv));
+            }
+          }
+        }
+        r -= Sb;
+        row[u] = r;
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+          v[u][c] = nxt[u][c];
+          const int64_t rn = r - Sb;
+          nxt[u][c] = (rn >= 0 && c < ncol) ? Yo[(int64_t)(c0 + c) * a.ldy + rn] : zero;
+        }
+        // a refilled row lies below every column of this block's band: no update; with
+        // kv < NB it can already be a head row of the next block
+        if (r > j0 - 2 * NB)
+#pragma unroll
+          for (int c = 0; c < NC; ++c) hd[(int)(j0 - NB - r) * NC + c] = v[u][c];
+      } else {
+        // d = (j0 - s2) - r in [1, kv] selects the band entries of this row
+        const int base = (int)(j0 - r);
+#pragma unroll
+        for (int s2 = 0; s2 < NB; ++s2) {
+          const int d = base - s2;
+          if (d >= 1 && d <= kv) {
+            const CT uu = Ust[(size_t)(NB - 1 - s2) * kvp + kv - d];
+#pragma unroll
+            for (int c = 0; c < NC; ++c) v[u][c] = cfms(uu, xs[s2 * NC + c], v[u][c]);
+          }
+        }
+        if (r > j0 - 2 * NB)
+#pragma unroll
+          for (int c = 0; c < NC; ++c) hd[(int)(j0 - NB - r) * NC + c] = v[u][c];
+      }
+    }
+  }
+  __syncthreads();
+  if (failed) {
+    if (tid == 0) atomicExch(a.status + ST_TIMEOUT, 1);
+    for (int st = 0; st < a.nstage; ++st)
+      for (int ph = 0; ph < 2; ++ph) mbar_wait_bounded(smem_u32(&mbar[st]), (uint32_t)ph);
+  }
+}
+
+template <typename CT, int NC, int SPT, int REGS>
+static cudaError_t launch_solve_r(const SolveArgsT<CT>& a, int q, int threads, size_t smem,
+                                  cudaStream_t s) {
+  auto kfn = band_solve_kernel<CT, NC, SPT, REGS>;
+  cudaError_t e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  int blocks = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, kfn, threads, smem);
+  if (e != cudaSuccess) return e;
+  if (blocks < 1) return cudaErrorLaunchOutOfResources;   // refuse rather than fail the launch
+  dim3 grid((unsigned)((a.k + NC - 1) / NC), (unsigned)q);
+  kfn<<<grid, threads, smem, s>>>(a); ie_count_launch();
+  return cudaGetLastError();
+}
+
+template <typename CT, int NC, int SPT>
+static cudaError_t launch_solve_t(const SolveArgsT<CT>& a, int q, int threads, size_t smem,
+                                  cudaStream_t s) {
+  if (threads <= 16 * 32) return launch_solve_r<CT, NC, SPT, 112>(a, q, threads, smem, s);
+  return launch_solve_r<CT, NC, SPT, 96>(a, q, threads, smem, s);
+}
+
+// threads, stages and shared memory for a solve with element type CT; returns false if the
+// band is too wide for one CTA
+template <typename CT>
+static bool solve_shape(SolveArgsT<CT>& a, int* threads, int* spt, size_t* smem) {
+  const int slots = a.kv + NB;                // backward window (larger than kl + NB)
+  *spt = slots > 576 ? 2 : 1;
+  if (slots > 1152) return false;              // half bandwidth up to 572
+  *threads = ((slots + *spt - 1) / *spt + 31) / 32 * 32;
+  const size_t stage_bytes =
+      (((size_t)NB * a.kvp * sizeof(CT) + NB * sizeof(CT)) + 127) & ~(size_t)127;
+  const size_t fixed = 128 + (4 * 8 + 4 * NB * 8) * sizeof(CT) + 256;
+  const size_t budget = 200 * 1024;
+  int nstage = (int)((budget - fixed) / stage_bytes);
+  if (nstage > 6) nstage = 6;
+  if (nstage < 2) return false;
+  a.nstage = nstage;
+  *smem = fixed + (size_t)nstage * stage_bytes;
+  return true;
+}
+
+static int pick_nc(int q, int k, int sms, int ncmax) {
+  // the smallest NC that keeps q * ceil(k/NC) CTAs within one wave
+  for (int c = 1; c <= ncmax; c *= 2)
+    if ((int64_t)q * ((k + c - 1) / c) <= sms) return c;
+  return ncmax;
+}
+
+cudaError_t launch_band_solve(int q, int64_t n, int kl, int ldab, int64_t n_pad, const cplx* AB,
+                              const int* piv, const cplx* dinv, const cplx* d_weights,
+                              const cplx* RHS, int64_t ldr, int k, cplx* Xp, int64_t ldx,
+                              int64_t xstride, int* status, cudaStream_t s) {
+  if (k <= 0) return cudaSuccess;
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  SolveArgsT<cplx> a{};
+  a.n = n; a.n_pad = n_pad; a.kl = kl; a.kv = 2 * kl; a.klp = kl; a.kvp = 2 * kl; a.k = k;
+  a.mode = 0;
+  a.L = AB + a.kv + 1; a.U = AB; a.ldl = ldab; a.ldu = ldab;
+  a.lstride = n_pad * ldab; a.ustride = n_pad * ldab;
+  a.piv = piv; a.dinv = dinv; a.weights = d_weights;
+  a.RHS = RHS; a.ldr = ldr; a.rstride = 0;
+  a.Y = Xp; a.ldy = ldx; a.ystride = xstride;
+  a.X = Xp; a.ldx = ldx; a.xstride = xstride;
+  a.status = status;
+  int threads, spt;
+  size_t smem;
+  if (!solve_shape(a, &threads, &spt, &smem)) return cudaErrorInvalidValue;
+  int NC = pick_nc(q, k, sms, 4);
+  if (NC == 8) NC = 4;
+  if (spt == 1) {
+    switch (NC) {
+      case 1: return launch_solve_t<cplx, 1, 1>(a, q, threads, smem, s);
+      case 2: return launch_solve_t<cplx, 2, 1>(a, q, threads, smem, s);
+      default: return launch_solve_t<cplx, 4, 1>(a, q, threads, smem, s);
+    }
+  }
+  switch (NC) {
+    case 1: return launch_solve_t<cplx, 1, 2>(a, q, threads, smem, s);
+    default: return launch_solve_t<cplx, 2, 2>(a, q, threads, smem, s);
+  }
+}
+
+cudaError_t launch_band_solve32(int q, int64_t n, int kl, int64_t n_pad, const float2* L32,
+                                int64_t ldl, const float2* U32, int64_t ldu, const int* piv,
+                                const float2* dinv32, const cplx* d_weights, const float2* RHS,
+                                int64_t ldr, int64_t rstride, int k, float2* Y32, int64_t ldy,
+                                int64_t ystride, cplx* X, int64_t ldx, int64_t xstride,
+                                int accumulate, int* status, cudaStream_t s) {
+  if (k <= 0) return cudaSuccess;
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  SolveArgsT<float2> a{};
+  a.n = n; a.n_pad = n_pad; a.kl = kl; a.kv = 2 * kl;
+  a.klp = (int)ldl; a.kvp = (int)ldu;   // padded column lengths = column strides
+  a.k = k; a.mode = accumulate ? 2 : 1;
+  a.L = L32; a.U = U32; a.ldl = ldl; a.ldu = ldu;
+  a.lstride = n_pad * ldl; a.ustride = n_pad * ldu;
+  a.piv = piv; a.dinv = dinv32; a.weights = d_weights;
+  a.RHS = RHS; a.ldr = ldr; a.rstride = rstride;
+  a.Y = Y32; a.ldy = ldy; a.ystride = ystride;
+  a.X = X; a.ldx = ldx; a.xstride = xstride;
+  a.status = status;
+  int threads, spt;
+  size_t smem;
+  if (!solve_shape(a, &threads, &spt, &smem)) return cudaErrorInvalidValue;
+  // latency-bound in FP32: more columns per CTA amortise each row's barrier
+  const int NC = pick_nc(q, k, sms, 8);
+  if (spt == 1) {
+    switch (NC) {
+      case 1: return launch_solve_t<float2, 1, 1>(a, q, threads, smem, s);
+      case 2: return launch_solve_t<float2, 2, 1>(a, q, threads, smem, s);
+      case 4: return launch_solve_t<float2, 4, 1>(a, q, threads, smem, s);
+      default: return launch_solve_t<float2, 8, 1>(a, q, threads, smem, s);
+    }
+  }
+  switch (NC) {
+    case 1: return launch_solve_t<float2, 1, 2>(a, q, threads, smem, s);
+    case 2: return launch_solve_t<float2, 2, 2>(a, q, threads, smem, s);
+    default: return launch_solve_t<float2, 4, 2>(a, q, threads, smem, s);
+  }
+}

@@ -37,7 +37,8 @@ class ie_opts(C.Structure):
     _fields_ = [("k", C.c_int32), ("driver", C.c_int32), ("m_max", C.c_int32),
                 ("max_outer", C.c_int32), ("tau_g", C.c_double), ("tau", C.c_double),
                 ("gmres_tol", C.c_double), ("sigma_is_center", C.c_int32),
-                ("sigma_re", C.c_double), ("sigma_im", C.c_double), ("seed", C.c_uint64)]
+                ("sigma_re", C.c_double), ("sigma_im", C.c_double), ("seed", C.c_uint64),
+                ("precision", C.c_int32), ("refine_steps", C.c_int32)]
 
 
 class ie_stats(C.Structure):
@@ -47,7 +48,9 @@ class ie_stats(C.Structure):
                 ("t_filter_ms", C.c_double), ("t_hsrr_ms", C.c_double),
                 ("max_rho_found", C.c_double), ("solve_launches", C.c_int64),
                 ("t_solve_ms", C.c_double), ("solve_flops", C.c_double),
-                ("solve_bytes", C.c_double), ("kernel_launches", C.c_int64)]
+                ("solve_bytes", C.c_double), ("kernel_launches", C.c_int64),
+                ("solve32_launches", C.c_int64), ("t_solve32_ms", C.c_double),
+                ("solve32_flops", C.c_double)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}

@@ -46,9 +46,10 @@ def test_struct_layouts_match_header():
     import paper_2310_18043_gb300.ie as ie
     src = open(HEADER).read()
 
+    src_nc = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+
     def fields(name):
-        body = re.search(r"typedef struct \{([^{}]*)\}\s*" + name + ";", src).group(1)
-        body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
+        body = re.search(r"typedef struct \{([^{}]*)\}\s*" + name + ";", src_nc).group(1)
         out = []
         for decl in body.split(";"):
             decl = decl.strip()

@@ -1,0 +1,78 @@
+"""Mixed precision (opts.precision = 1): complex64 factors and FP32 band solves, each
+K_i^{-1} b refined in FP64. Same tolerances as the complex128 path: G(V) to 1e-11, the
+filtered block to 1e-9, eigenvalues in D to 1e-10 with rho <= 1e-10."""
+import numpy as np
+import pytest
+
+import ie_inputs
+from oracle import inner, msgmres
+
+from test_gpu_parity import Case, dblock, dzeros, golden_eigs, match_eigs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ie():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2310_18043_gb300 import build as b
+    b.build()
+    import paper_2310_18043_gb300.ie as ie_
+    return ie_
+
+
+def mixed(ie, name, **over):
+    over.setdefault("precision", 1)
+    return Case(ie, name, **over)
+
+
+@pytest.mark.parametrize("name,k", [("c1_m24", 16), ("r1_m37", 11), ("m1_m64", 24)])
+def test_mixed_apply_G_matches_oracle(ie, name, k):
+    c = mixed(ie, name)
+    try:
+        V = ie_inputs.random_block(c.n, k, seed=5)
+        GVd = dzeros(c.n, k)
+        assert ie.ie_apply_G(c.h, dblock(V), GVd) == ie.IE_OK
+        G = inner.InnerOperator(c.A, c.B, c.w["center"], c.w["radius"], c.w["q"])
+        ref = G.apply(V)
+        err = np.linalg.norm(GVd.cpu().numpy() - ref, axis=0) / np.linalg.norm(ref, axis=0)
+        assert err.max() < 1e-11, err.max()
+        _, st = ie.ie_get_stats(c.h)
+        assert st["solve32_launches"] == 1 + 2 and st["solve_launches"] == 0
+    finally:
+        c.close()
+
+
+def test_mixed_filter_matches_oracle(ie):
+    c = mixed(ie, "r1_m37")
+    try:
+        k = c.w["k"]
+        Y = ie_inputs.orthonormal_random_block(c.n, k, seed=2)
+        Ud = dzeros(c.n, k)
+        assert ie.ie_filter_apply(c.h, dblock(Y), Ud) == ie.IE_OK
+        G = inner.InnerOperator(c.A, c.B, c.w["center"], c.w["radius"], c.w["q"])
+        ref = msgmres.filter_apply(G, Y, c.w["p"], tol=1e-12, m_max=100)
+        err = np.linalg.norm(Ud.cpu().numpy() - ref) / np.linalg.norm(ref)
+        assert err < 1e-9, err
+    finally:
+        c.close()
+
+
+@pytest.mark.parametrize("name,driver", [("c1_m24", 1), ("r1_m37", 2), ("m1_m64", 1),
+                                         ("c2_m256", 2)])
+def test_mixed_solve_matches_golden(ie, name, driver):
+    c = mixed(ie, name, driver=driver, m_max=150)
+    try:
+        k = c.w["k"]
+        Y0 = ie_inputs.orthonormal_random_block(c.n, k, seed=c.w["seed"])
+        Xd = dzeros(c.n, k)
+        st, lam, rho, e, nf, stats = ie.ie_solve(c.h, dblock(Y0), Xd, k)
+        assert st == ie.IE_OK, ie.ie_status_str(st)
+        ref = golden_eigs(c.w)
+        assert nf == len(ref)
+        match_eigs(lam[:nf], ref)
+        assert np.all(rho[:nf] <= 1e-10)
+    finally:
+        c.close()
