@@ -43,6 +43,9 @@ def parse():
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--solve", type=int, default=1,
+                    help="1: also time one full ie_create + ie_solve per driver (time to all "
+                         "eigenpairs in D at residual 1e-10), outside the throughput steps")
     ap.add_argument("--precision", type=int, default=0, choices=[0, 1],
                     help="0: complex128 factors and solves; 1: complex64 factors, FP32 solves, "
                          "FP64 refinement")
@@ -212,6 +215,35 @@ def run_native(args):
     value = cols / (t_ms / 1e3)
     gpu_launches = int(sB["kernel_launches"] - sA["kernel_launches"])   # counted by libie
 
+    solves = None
+    if args.solve and rank == 0:
+        solves = {}
+        ie.ie_destroy(h)
+        h = None
+        ref = np.array(w["eig_in_disk_re"]) + 1j * np.array(w["eig_in_disk_im"])
+        for drv in (1, 2):
+            o = ie.ie_opts_default(k=k, m_max=150, precision=args.precision, driver=drv)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            st0, hs = ie.ie_create(n, pen.offsets, A_d, B_d, w["center"], w["radius"], p, q, o,
+                                   stream)
+            Y0 = ie_inputs.orthonormal_random_block(n, k, seed=w["seed"])
+            Y0d = torch.from_numpy(np.ascontiguousarray(Y0.T)).to(device).T
+            st1, lam, rho, e, nf, sst = ie.ie_solve(hs, Y0d, Xd, k, stream)
+            torch.cuda.synchronize()
+            tt = time.perf_counter() - t0
+            got = lam[:nf]
+            err = (float(np.max(np.min(np.abs(got[:, None] - ref[None, :]), axis=1) / np.abs(got)))
+                   if nf else None)
+            solves[f"alg{drv}"] = {
+                "seconds": tt, "status": ie.ie_status_str(st1), "n_found": nf,
+                "n_in_disk_reference": int(len(ref)), "max_rho": float(np.max(rho[:nf])) if nf else None,
+                "max_rel_err_vs_reference": err, "outer_iters": sst["outer_iters"],
+                "p_final": sst["p_final"], "factor_ms": sst["t_factor_ms"],
+                "filter_ms": sst["t_filter_ms"], "hsrr_ms": sst["t_hsrr_ms"]}
+            ie.ie_destroy(hs)
+        st, h = ie.ie_create(n, pen.offsets, A_d, B_d, w["center"], w["radius"], p, q, opts, stream)
+
     e2e = None
     if not args.no_e2e and rank == 0:
         Yh = torch.from_numpy(np.ascontiguousarray(Y.T)).pin_memory().numpy().T
@@ -270,6 +302,7 @@ def run_native(args):
                          "launches": launches, "avg_launch_ms": solve_ms / launches if launches else None,
                          "share_of_step": solve_ms / t_ms if t_ms > 0 else None},
             "gpu_launches": gpu_launches,
+            "time_to_all_eigenpairs": solves,
             "e2e": e2e,
             "clocks": clk.summary(),
             "cpu_baseline": cpu,

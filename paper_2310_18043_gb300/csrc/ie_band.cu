@@ -334,12 +334,16 @@ void launch_pole_wsum(int q, int64_t n, int k, const cplx* Xp, int64_t ldx, int6
 }
 
 // ----------------------------------------------------------------------------------------------
-// Mixed precision: complex64 copy of the factors in a layout whose column segments start on
-// 16-byte boundaries and have even lengths (bulk-copy rules): L32 column j = the kl L
-// multipliers padded to klp (even), U32 column j = U(j-kv..j-1, j) (kv = 2 kl entries),
-// dinv32 = 1/u_jj. Rounded from the FP64 factorisation.
-__global__ void factors_to_c64_kernel(int64_t n_pad, int kl, int ldab, int klp, const cplx* AB,
-                                      const cplx* dinv, float2* L32, float2* U32, float2* dinv32) {
+// Split factor layout for the solves: L column j = its kl multipliers (padded to klp), U column
+// j = U(j-kv..j-1, j) (kv = 2 kl entries), columns contiguous per pole so that a panel of 8
+// columns is one bulk copy with 16-byte aligned start and length. complex128 (from the LU in
+// LAPACK band storage) or complex64 rounded from it (mixed precision, with 1/u_jj).
+__device__ __forceinline__ void put_c(float2* p, cplx v) { *p = make_float2((float)v.x, (float)v.y); }
+__device__ __forceinline__ void put_c(cplx* p, cplx v) { *p = v; }
+
+template <typename OT>
+__global__ void factors_split_kernel(int64_t n_pad, int kl, int ldab, int klp, const cplx* AB,
+                                     const cplx* dinv, OT* L32, OT* U32, OT* dinv32) {
   const int pole = blockIdx.y;
   const int kv = 2 * kl;
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -349,14 +353,11 @@ __global__ void factors_to_c64_kernel(int64_t n_pad, int kl, int ldab, int klp, 
   const int t = (int)(idx - j * per);
   const cplx* col = AB + ((int64_t)pole * n_pad + j) * ldab;
   if (t < klp) {
-    const cplx v = (t < kl) ? col[kv + 1 + t] : cmk(0, 0);
-    L32[((int64_t)pole * n_pad + j) * klp + t] = make_float2((float)v.x, (float)v.y);
+    put_c(&L32[((int64_t)pole * n_pad + j) * klp + t], (t < kl) ? col[kv + 1 + t] : cmk(0, 0));
   } else if (t < klp + kv) {
-    const cplx v = col[t - klp];
-    U32[((int64_t)pole * n_pad + j) * kv + (t - klp)] = make_float2((float)v.x, (float)v.y);
-  } else {
-    const cplx v = dinv[(int64_t)pole * n_pad + j];
-    dinv32[(int64_t)pole * n_pad + j] = make_float2((float)v.x, (float)v.y);
+    put_c(&U32[((int64_t)pole * n_pad + j) * kv + (t - klp)], col[t - klp]);
+  } else if (dinv32) {
+    put_c(&dinv32[(int64_t)pole * n_pad + j], dinv[(int64_t)pole * n_pad + j]);
   }
 }
 
@@ -365,7 +366,14 @@ void launch_factors_to_c64(int q, int64_t n_pad, int kl, int ldab, int klp, cons
                            cudaStream_t s) {
   const int64_t tot = n_pad * (klp + 2 * kl + 1);
   dim3 grid((unsigned)((tot + 255) / 256), (unsigned)q);
-  factors_to_c64_kernel<<<grid, 256, 0, s>>>(n_pad, kl, ldab, klp, AB, dinv, L32, U32, dinv32); ie_count_launch();
+  factors_split_kernel<float2><<<grid, 256, 0, s>>>(n_pad, kl, ldab, klp, AB, dinv, L32, U32, dinv32); ie_count_launch();
+}
+
+void launch_factors_split64(int q, int64_t n_pad, int kl, int ldab, const cplx* AB, cplx* L64,
+                            cplx* U64, cudaStream_t s) {
+  const int64_t tot = n_pad * (kl + 2 * kl + 1);
+  dim3 grid((unsigned)((tot + 255) / 256), (unsigned)q);
+  factors_split_kernel<cplx><<<grid, 256, 0, s>>>(n_pad, kl, ldab, kl, AB, nullptr, L64, U64, (cplx*)nullptr); ie_count_launch();
 }
 
 // R32[i][:, c] = (complex64) (BV[:, c] - K_i X[i][:, c]), K_i = p_i B - A, for all poles i:

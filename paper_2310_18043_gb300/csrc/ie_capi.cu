@@ -67,6 +67,13 @@ struct ie_handle_s {
   cplx* AB = nullptr;
   int* piv = nullptr;
   cplx* dinv = nullptr;
+  cplx* L64 = nullptr;     // q * n_pad * kl: split complex128 L multipliers
+  cplx* U64 = nullptr;     // q * n_pad * kv: split complex128 U columns
+  cplx* Tb = nullptr;      // q * npanel * 256: forward block transforms
+  int* Hb = nullptr;       // q * npanel * 16: their member rows
+  cplx* Uinvb = nullptr;   // q * npanel * 64: inverses of U's 8x8 diagonal blocks
+  float2* T32 = nullptr;   // complex64 copies (precision = 1)
+  float2* Ub32 = nullptr;
   unsigned* bar = nullptr;
   int* status = nullptr;
   int lu_ctas = 0;
@@ -397,6 +404,24 @@ extern "C" ie_status ie_create(const ie_pencil* pen, ie_complex center, double r
   int st[ST_COUNT];
   cudaMemcpy(st, h->status, sizeof(st), cudaMemcpyDeviceToHost);
   if (st[ST_TIMEOUT]) return fail(IE_ERR_TIMEOUT);
+  {
+    const size_t np = (size_t)(h->n_pad / 8);
+    if (h->alloc(&h->L64, (size_t)q * h->n_pad * kl) != cudaSuccess ||
+        h->alloc(&h->U64, (size_t)q * h->n_pad * h->kv) != cudaSuccess)
+      return fail(IE_ERR_OOM);
+    launch_factors_split64(q, h->n_pad, kl, h->ldab, h->AB, h->L64, h->U64, s);
+    if (h->alloc(&h->Tb, (size_t)q * np * 256) != cudaSuccess ||
+        h->alloc(&h->Hb, (size_t)q * np * 16) != cudaSuccess ||
+        h->alloc(&h->Uinvb, (size_t)q * np * 64) != cudaSuccess)
+      return fail(IE_ERR_OOM);
+    if (opts.precision == 1 &&
+        (h->alloc(&h->T32, (size_t)q * np * 256) != cudaSuccess ||
+         h->alloc(&h->Ub32, (size_t)q * np * 64) != cudaSuccess))
+      return fail(IE_ERR_OOM);
+    launch_block_transforms(q, h->n, h->n_pad, kl, h->ldab, h->AB, h->piv, h->dinv, h->Tb, h->Hb,
+                            h->Uinvb, h->T32, h->Ub32, s);
+    if (cudaStreamSynchronize(s) != cudaSuccess) return fail(IE_ERR_CUDA);
+  }
   ie_status ws = alloc_workspace(h);
   if (ws != IE_OK) return fail(ws);
   if (h->precision == 1) {
@@ -498,8 +523,9 @@ static ie_status apply_G_dev(ie_handle h, const cplx* V, int64_t ldv, const int6
     rec.fp32 = 0;
   }
   cudaEventRecord(rec.a, s);
-  CK(launch_band_solve(h->q, h->n, h->kl, h->ldab, h->n_pad, h->AB, h->piv, h->dinv, h->d_weights,
-                       h->BVw, h->n, k, h->Xp, h->n, h->n * (int64_t)h->kmax, h->status, s));
+  CK(launch_band_solve(h->q, h->n, h->kl, h->n_pad, h->L64, h->U64, h->piv, h->dinv, h->Tb, h->Hb,
+                       h->Uinvb, h->d_weights, h->BVw, h->n, k, h->Xp, h->n, h->n * (int64_t)h->kmax,
+                       h->status, s));
   cudaEventRecord(rec.b, s);
   h->pending.push_back(rec);
   launch_pole_sum(h->q, h->n, k, h->Xp, h->n, h->n * (int64_t)h->kmax, GV, ldg, s);
@@ -527,7 +553,8 @@ static ie_status apply_G_mixed(ie_handle h, int k, cplx* GV, int64_t ldg, cudaSt
     rec.fp32 = 1;
     cudaEventRecord(rec.a, s);
     CK(launch_band_solve32(h->q, n, h->kl, h->n_pad, h->L32, h->klp, h->U32, h->kv, h->piv,
-                           h->dinv32, h->d_weights, it == 0 ? h->BV32 : h->R32, n,
+                           h->dinv32, h->T32, h->Hb, h->Ub32, h->d_weights,
+                           it == 0 ? h->BV32 : h->R32, n,
                            it == 0 ? 0 : ps, k, h->Y32, n, ps, h->Xp, n, ps, it > 0 ? 1 : 0,
                            h->status, s));
     cudaEventRecord(rec.b, s);
@@ -955,8 +982,13 @@ bool ie_internal_factors(ie_handle h, IeFactorsView* v) {
   v->ldab = h->ldab;
   v->q = h->q;
   v->AB = h->AB;
+  v->L64 = h->L64;
+  v->U64 = h->U64;
   v->piv = h->piv;
   v->dinv = h->dinv;
+  v->Tb = h->Tb;
+  v->Hb = h->Hb;
+  v->Ub = h->Uinvb;
   v->weights = h->d_weights;
   v->status = h->status;
   return true;

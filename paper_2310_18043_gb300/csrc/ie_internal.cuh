@@ -92,18 +92,31 @@ cudaError_t launch_band_lu(int q, int64_t n, int kl, int ldab, int64_t n_pad, cp
                            int* ctas_per_pole);
 // Forward (P, L) then backward (U) band solves for all q poles and k RHS columns;
 // Xp[i] (n x k, ld = ldx, pole stride xstride) = w_i K_i^{-1} RHS.
-cudaError_t launch_band_solve(int q, int64_t n, int kl, int ldab, int64_t n_pad, const cplx* AB,
-                              const int* piv, const cplx* dinv, const cplx* d_weights,
-                              const cplx* RHS, int64_t ldr, int k, cplx* Xp, int64_t ldx,
-                              int64_t xstride, int* status, cudaStream_t s);
+// L64/U64: the split complex128 factors (launch_factors_split64); Tb/Hb/Ub: the per-panel
+// block transforms of launch_block_transforms.
+cudaError_t launch_band_solve(int q, int64_t n, int kl, int64_t n_pad, const cplx* L64,
+                              const cplx* U64,
+                              const int* piv, const cplx* dinv, const cplx* Tb, const int* Hb,
+                              const cplx* Ub, const cplx* d_weights, const cplx* RHS, int64_t ldr,
+                              int k, cplx* Xp, int64_t ldx, int64_t xstride, int* status,
+                              cudaStream_t s);
+// Per (pole, 8-column panel): forward 16x16 transform T with its member rows H, backward
+// inverse of the 8x8 diagonal block of U (complex128; complex64 copies when T32/Ui32 != null).
+void launch_block_transforms(int q, int64_t n, int64_t n_pad, int kl, int ldab, const cplx* AB,
+                             const int* piv, const cplx* dinv, cplx* T, int* H, cplx* Ui,
+                             float2* T32, float2* Ui32, cudaStream_t s);
 // Mixed precision: complex64 band solves; X (FP64, per pole) = x (accumulate = 0) or += x.
 // RHS column c of pole i at RHS + i*rstride + c*ldr (rstride 0: shared right-hand side).
 cudaError_t launch_band_solve32(int q, int64_t n, int kl, int64_t n_pad, const float2* L32,
                                 int64_t ldl, const float2* U32, int64_t ldu, const int* piv,
-                                const float2* dinv32, const cplx* d_weights, const float2* RHS,
+                                const float2* dinv32, const float2* T32, const int* Hb,
+                                const float2* Ui32, const cplx* d_weights, const float2* RHS,
                                 int64_t ldr, int64_t rstride, int k, float2* Y32, int64_t ldy,
                                 int64_t ystride, cplx* X, int64_t ldx, int64_t xstride,
                                 int accumulate, int* status, cudaStream_t s);
+// complex128 split copy: L64 (n_pad x kl per pole), U64 (n_pad x 2kl per pole)
+void launch_factors_split64(int q, int64_t n_pad, int kl, int ldab, const cplx* AB, cplx* L64,
+                            cplx* U64, cudaStream_t s);
 void launch_factors_to_c64(int q, int64_t n_pad, int kl, int ldab, int klp, const cplx* AB,
                            const cplx* dinv, float2* L32, float2* U32, float2* dinv32,
                            cudaStream_t s);
@@ -193,8 +206,13 @@ struct IeFactorsView {
   int64_t n, n_pad;
   int kl, ldab, q;
   const cplx* AB;
+  const cplx* L64;
+  const cplx* U64;
   const int* piv;
   const cplx* dinv;
+  const cplx* Tb;
+  const int* Hb;
+  const cplx* Ub;
   const cplx* weights;
   int* status;
 };

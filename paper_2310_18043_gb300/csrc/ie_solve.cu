@@ -61,6 +61,9 @@ __device__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity) {
 __device__ __forceinline__ float2 cfms(float2 a, float2 b, float2 c) {
   return make_float2(fmaf(-a.x, b.x, fmaf(a.y, b.y, c.x)), fmaf(-a.x, b.y, fmaf(-a.y, b.x, c.y)));
 }
+__device__ __forceinline__ float2 cfma(float2 a, float2 b, float2 c) {
+  return make_float2(fmaf(a.x, b.x, fmaf(-a.y, b.y, c.x)), fmaf(a.x, b.y, fmaf(a.y, b.x, c.y)));
+}
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
   return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
 }
@@ -78,13 +81,19 @@ template <typename CT>
 struct SolveArgsT {
   int64_t n, n_pad;
   int kl, kv, klp, kvp, k, nstage, mode;
-  // factors: column col's L part (kl entries, padded to klp) at L + pole*lstride + col*ldl,
-  // U part (rows col-kv..col-1, padded to kvp) at U + pole*ustride + col*ldu
+  // factors, split and contiguous: column col's L part (kl entries, padded to klp) at
+  // L + pole*lstride + col*ldl with ldl = klp, U part (rows col-kv..col-1, kvp = kv entries)
+  // at U + pole*ustride + col*ldu with ldu = kvp
   const CT* L;
   const CT* U;
   int64_t ldl, ldu, lstride, ustride;
   const int* piv;     // 0-based, pole stride n_pad
   const CT* dinv;     // 1/u_jj, pole stride n_pad
+  // per (pole, panel) block transforms (see block_transform_kernel): forward 16x16 T and its
+  // member rows, backward 8x8 inverse of U's diagonal block
+  const CT* Tb;       // [pole][panel][16][16]
+  const int* Hb;      // [pole][panel][16]
+  const CT* Ub;       // [pole][panel][8][8]
   const cplx* weights;
   const CT* RHS;      // column c at RHS + pole*rstride + c*ldr
   int64_t ldr, rstride;
@@ -110,6 +119,10 @@ __global__ void __maxnreg__(REGS) band_solve_kernel(SolveArgsT<CT> a) {
   const CT* Up = a.U + (int64_t)pole * a.ustride;
   const int* pivp = a.piv + (int64_t)pole * a.n_pad;
   const CT* dinvp = a.dinv + (int64_t)pole * a.n_pad;
+  const int64_t npan = a.n_pad / NB;
+  const CT* Tp = a.Tb + (int64_t)pole * npan * 256;
+  const int* Hp = a.Hb + (int64_t)pole * npan * 16;
+  const CT* Uip = a.Ub + (int64_t)pole * npan * 64;
   const CT* R = a.RHS + (int64_t)pole * a.rstride;
   CT* Yo = a.Y + (int64_t)pole * a.ystride;
   cplx* Xo = a.X + (int64_t)pole * a.xstride;
@@ -121,11 +134,14 @@ __global__ void __maxnreg__(REGS) band_solve_kernel(SolveArgsT<CT> a) {
   CT* bc = (CT*)(sm_raw + 128);                                // [2][2][NC] broadcast cells
   CT* hd = bc + 4 * NC;                                        // [NB][NC] head values
   CT* xs = hd + NB * NC;                                       // [NB][NC] solved head
-  CT* hv = xs + NB * NC;                                       // [2NB][NC] forward block set
-  unsigned char* stage0 = (unsigned char*)(((uintptr_t)(hv + 2 * NB * NC) + 127) & ~(uintptr_t)127);
+  CT* hv = xs + NB * NC;                                       // [16][NC] forward set H
+  CT* hv2 = hv + 16 * NC;                                      // [16][NC] T H
+  unsigned char* stage0 = (unsigned char*)(((uintptr_t)(hv2 + 16 * NC) + 127) & ~(uintptr_t)127);
   const size_t fwd_cols_bytes = (size_t)NB * klp * sizeof(CT);
   const size_t bwd_cols_bytes = (size_t)NB * kvp * sizeof(CT);
-  const size_t stage_bytes = ((bwd_cols_bytes + NB * sizeof(CT)) + 127) & ~(size_t)127;
+  const size_t fwd_bytes = fwd_cols_bytes + 256 * sizeof(CT) + 16 * sizeof(int);
+  const size_t bwd_bytes = bwd_cols_bytes + 64 * sizeof(CT);
+  const size_t stage_bytes = ((fwd_bytes > bwd_bytes ? fwd_bytes : bwd_bytes) + 127) & ~(size_t)127;
   __shared__ int s_fail;
 
   if (tid == 0) {
@@ -137,103 +153,113 @@ __global__ void __maxnreg__(REGS) band_solve_kernel(SolveArgsT<CT> a) {
 
   const int64_t npanel = a.n_pad / NB;
   // ------------------------------- forward: P L y = rhs -------------------------------------
+  // Block = panel P, steps j0..j0+NB-1 (j0 = P*NB). Window of Sf = kl + NB rows j0..j0+Sf-1
+  // (slot = row mod Sf). Within a block only the NB head rows and the block's pivot rows take
+  // part in swaps; on that set H (16 members) the block's swaps and eliminations are the fixed
+  // 16x16 matrix T (precomputed from the factors), so: (A) gather H, (B) H <- T H in
+  // parallel, (C) head rows leave with y, pivot members take their values, every other row
+  // applies the block's NB multipliers at once. Three barriers per NB rows.
   auto issue_fwd = [&](int64_t P, int st) {
     unsigned char* dst = stage0 + (size_t)st * stage_bytes;
     const uint32_t bar = smem_u32(&mbar[st]);
-    mbar_expect_tx(bar, (uint32_t)(fwd_cols_bytes + NB * sizeof(int)));
-    for (int jj = 0; jj < NB; ++jj)
-      bulk_g2s(smem_u32(dst + (size_t)jj * klp * sizeof(CT)), Lp + (P * NB + jj) * a.ldl,
-               (uint32_t)(klp * sizeof(CT)), bar);
-    bulk_g2s(smem_u32(dst + fwd_cols_bytes), pivp + P * NB, (uint32_t)(NB * sizeof(int)), bar);
+    mbar_expect_tx(bar, (uint32_t)(fwd_cols_bytes + 256 * sizeof(CT) + 16 * sizeof(int)));
+    // the panel's NB columns are contiguous (ldl = klp): one copy
+    bulk_g2s(smem_u32(dst), Lp + P * NB * a.ldl, (uint32_t)fwd_cols_bytes, bar);
+    bulk_g2s(smem_u32(dst + fwd_cols_bytes), Tp + P * 256, (uint32_t)(256 * sizeof(CT)), bar);
+    bulk_g2s(smem_u32(dst + fwd_cols_bytes + 256 * sizeof(CT)), Hp + P * 16,
+             (uint32_t)(16 * sizeof(int)), bar);
   };
-  const int S = kl + 1;
+  const int Sf = kl + NB;
   CT v[SPT][NC], nxt[SPT][NC];
-  int off[SPT];
+  int64_t frow[SPT];
   if (tid == 0)
     for (int st = 0; st < a.nstage && st < npanel; ++st) issue_fwd(st, st);
-  {
-    const int p0 = __ldg(pivp);
+#pragma unroll
+  for (int u = 0; u < SPT; ++u) {
+    const int s = tid + u * T;
+    frow[u] = s;
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      v[u][c] = (s < Sf && s < n && c < ncol) ? R[(int64_t)(c0 + c) * a.ldr + s] : zero;
+      nxt[u][c] = (s < Sf && s + Sf < n && c < ncol) ? R[(int64_t)(c0 + c) * a.ldr + s + Sf] : zero;
+    }
+  }
+  bool failed = false;
+  for (int64_t P = 0; P < npanel && !failed; ++P) {
+    const int st = (int)(P % a.nstage);
+    if (!mbar_wait_bounded(smem_u32(&mbar[st]), (uint32_t)((P / a.nstage) & 1))) s_fail = 1;
+    __syncthreads();
+    if (s_fail) { failed = true; break; }
+    // the previous panel's stage is free: refill it
+    if (tid == 0 && P >= 1 && P - 1 + a.nstage < npanel)
+      issue_fwd(P - 1 + a.nstage, (int)((P - 1) % a.nstage));
+    const CT* Lst = (const CT*)(stage0 + (size_t)st * stage_bytes);
+    const CT* Tst = (const CT*)(stage0 + (size_t)st * stage_bytes + fwd_cols_bytes);
+    const int* Hst = (const int*)(stage0 + (size_t)st * stage_bytes + fwd_cols_bytes + 256 * sizeof(CT));
+    const int64_t j0 = P * NB;
+    const int nvalid = (int)((n - j0) < NB ? (n - j0) : NB);
+    // (A) gather the members' values
 #pragma unroll
     for (int u = 0; u < SPT; ++u) {
       const int s = tid + u * T;
-      off[u] = s;
-      const int64_t r = s;
+      if (s >= Sf) continue;
+      const int64_t r = frow[u];
+      for (int i = 0; i < 16; ++i)
+        if (Hst[i] == r) {
 #pragma unroll
-      for (int c = 0; c < NC; ++c) {
-        v[u][c] = (s < S && r < n && c < ncol) ? R[(int64_t)(c0 + c) * a.ldr + r] : zero;
-        nxt[u][c] = (s < S && r + S < n && c < ncol) ? R[(int64_t)(c0 + c) * a.ldr + r + S] : zero;
+          for (int c = 0; c < NC; ++c) hv[i * NC + c] = v[u][c];
+        }
+    }
+    __syncthreads();
+    // (B) H <- T H
+    for (int e = tid; e < 16 * NC; e += T) {
+      const int i = e / NC, c = e - (e / NC) * NC;
+      if (Hst[i] >= 0) {
+        CT acc = zero;
+        for (int m = 0; m < 16; ++m)
+          if (Hst[m] >= 0) acc = cfma(Tst[i * 16 + m], hv[m * NC + c], acc);
+        hv2[i * NC + c] = acc;
       }
-      if (s < S) {
-        if (r == p0)
+    }
+    __syncthreads();
+    // (C)
 #pragma unroll
-          for (int c = 0; c < NC; ++c) bc[c] = v[u][c];
-        if (r == 0)
+    for (int u = 0; u < SPT; ++u) {
+      const int s = tid + u * T;
+      if (s >= Sf) continue;
+      const int64_t r = frow[u];
+      int i = -1;
+      for (int m = 0; m < 16; ++m)
+        if (Hst[m] == r) i = m;
+      if (i >= 0 && i < NB) {
+        if (r < n)
 #pragma unroll
-          for (int c = 0; c < NC; ++c) bc[NC + c] = v[u][c];
+          for (int c = 0; c < NC; ++c)
+            if (c < ncol) Yo[(int64_t)(c0 + c) * a.ldy + r] = hv2[i * NC + c];
+        const int64_t r2 = r + Sf;
+        frow[u] = r2;
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+          v[u][c] = nxt[u][c];
+          nxt[u][c] = (r2 + Sf < n && c < ncol) ? R[(int64_t)(c0 + c) * a.ldr + r2 + Sf] : zero;
+        }
+      } else if (i >= NB) {
+#pragma unroll
+        for (int c = 0; c < NC; ++c) v[u][c] = hv2[i * NC + c];
+      } else {
+#pragma unroll
+        for (int jj = 0; jj < NB; ++jj) {
+          const int64_t j = j0 + jj;
+          if (jj < nvalid && r > j && r <= j + kl) {
+            const CT lv = Lst[(size_t)jj * klp + (r - j - 1)];
+#pragma unroll
+            for (int c = 0; c < NC; ++c) v[u][c] = cfms(lv, hv2[jj * NC + c], v[u][c]);
+          }
+        }
       }
     }
   }
   __syncthreads();
-  bool failed = false;
-  for (int64_t P = 0; P < npanel && !failed; ++P) {
-    const int st = (int)(P % a.nstage);
-    const int pnext = (P + 1 < npanel) ? __ldg(pivp + (P + 1) * NB) : -1;   // prefetched
-    if (!mbar_wait_bounded(smem_u32(&mbar[st]), (uint32_t)((P / a.nstage) & 1))) s_fail = 1;
-    __syncthreads();
-    if (s_fail) { failed = true; break; }
-    const CT* Lst = (const CT*)(stage0 + (size_t)st * stage_bytes);
-    const int* pst = (const int*)(stage0 + (size_t)st * stage_bytes + fwd_cols_bytes);
-    for (int jj = 0; jj < NB; ++jj) {
-      const int64_t j = P * NB + jj;
-      if (j >= n) break;
-      const int par = (int)(j & 1);
-      CT x[NC], xj[NC];
-#pragma unroll
-      for (int c = 0; c < NC; ++c) {
-        x[c] = bc[par * 2 * NC + c];
-        xj[c] = bc[par * 2 * NC + NC + c];
-      }
-      const int64_t jp = pst[jj];
-      const int64_t jp1 = (j + 1 < n) ? ((jj + 1 < NB) ? pst[jj + 1] : pnext) : -1;
-      const CT* Lc = Lst + (size_t)jj * klp;
-#pragma unroll
-      for (int u = 0; u < SPT; ++u) {
-        const int s = tid + u * T;
-        if (s >= S) continue;
-        const int o = off[u];
-        int64_t rnew;
-        if (o == 0) {
-          // row j leaves: y_j = x; the slot is refilled with row j + S
-#pragma unroll
-          for (int c = 0; c < NC; ++c)
-            if (c < ncol) Yo[(int64_t)(c0 + c) * a.ldy + j] = x[c];
-          rnew = j + S;
-#pragma unroll
-          for (int c = 0; c < NC; ++c) {
-            v[u][c] = nxt[u][c];
-            nxt[u][c] = (rnew + S < n && c < ncol) ? R[(int64_t)(c0 + c) * a.ldr + rnew + S] : zero;
-          }
-          off[u] = S - 1;
-        } else {
-          const int64_t r = j + o;
-          const CT l = Lc[o - 1];
-#pragma unroll
-          for (int c = 0; c < NC; ++c) v[u][c] = cfms(l, x[c], (r == jp) ? xj[c] : v[u][c]);
-          off[u] = o - 1;
-          rnew = r;
-        }
-        const int npar = par ^ 1;
-        if (rnew == jp1)
-#pragma unroll
-          for (int c = 0; c < NC; ++c) bc[npar * 2 * NC + c] = v[u][c];
-        if (rnew == j + 1)
-#pragma unroll
-          for (int c = 0; c < NC; ++c) bc[npar * 2 * NC + NC + c] = v[u][c];
-      }
-      __syncthreads();
-    }
-    if (tid == 0 && P + a.nstage < npanel) issue_fwd(P + a.nstage, st);
-  }
   if (failed) {
     if (tid == 0) atomicExch(a.status + ST_TIMEOUT, 1);
     for (int st = 0; st < a.nstage; ++st)
@@ -258,11 +284,10 @@ __global__ void __maxnreg__(REGS) band_solve_kernel(SolveArgsT<CT> a) {
     unsigned char* dst = stage0 + (size_t)st * stage_bytes;
     const uint32_t bar = smem_u32(&mbar[st]);
     const int64_t cb0 = a.n_pad - (Bp + 1) * NB;
-    mbar_expect_tx(bar, (uint32_t)(bwd_cols_bytes + NB * sizeof(CT)));
-    for (int jj = 0; jj < NB; ++jj)
-      bulk_g2s(smem_u32(dst + (size_t)jj * kvp * sizeof(CT)), Up + (cb0 + jj) * a.ldu,
-               (uint32_t)(kvp * sizeof(CT)), bar);
-    bulk_g2s(smem_u32(dst + bwd_cols_bytes), dinvp + cb0, (uint32_t)(NB * sizeof(CT)), bar);
+    mbar_expect_tx(bar, (uint32_t)(bwd_cols_bytes + 64 * sizeof(CT)));
+    bulk_g2s(smem_u32(dst), Up + cb0 * a.ldu, (uint32_t)bwd_cols_bytes, bar);   // contiguous
+    bulk_g2s(smem_u32(dst + bwd_cols_bytes), Uip + (cb0 / NB) * 64, (uint32_t)(64 * sizeof(CT)),
+             bar);
   };
   const int Sb = kv + NB;
   int64_t row[SPT];
@@ -296,17 +321,17 @@ __global__ void __maxnreg__(REGS) band_solve_kernel(SolveArgsT<CT> a) {
     if (tid == 0 && Bp >= 1 && Bp - 1 + a.nstage < npanel)
       issue_bwd(Bp - 1 + a.nstage, (int)((Bp - 1) % a.nstage));
     const CT* Ust = (const CT*)(stage0 + (size_t)st * stage_bytes);
-    const CT* dst_ = (const CT*)(stage0 + (size_t)st * stage_bytes + bwd_cols_bytes);
+    const CT* Uist = (const CT*)(stage0 + (size_t)st * stage_bytes + bwd_cols_bytes);
     const int64_t j0 = a.n_pad - 1 - Bp * NB;
-    // head rows j0 - t (t = 0..NB-1); matrix column j0 - s2 is stage column NB-1-s2
-    if (tid < NC) {
-      const int c = tid;
-      for (int t = 0; t < NB; ++t) {
-        CT acc = hd[t * NC + c];
-        for (int s2 = (t - kv > 0 ? t - kv : 0); s2 < t; ++s2)   // band: t - s2 <= kv
-          acc = cfms(Ust[(size_t)(NB - 1 - s2) * kvp + kv - (t - s2)], xs[s2 * NC + c], acc);
-        xs[t * NC + c] = cmul(acc, dst_[NB - 1 - t]);
-      }
+    // head rows j0 - t (t = 0..NB-1) = block rows NB-1-t; matrix column j0 - s2 is stage
+    // column NB-1-s2. x_head = inv(U_block) h_head, one (row, column) per thread.
+    for (int e = tid; e < NB * NC; e += T) {
+      const int t = e / NC, c = e - (e / NC) * NC;
+      CT acc = zero;
+#pragma unroll
+      for (int t2 = 0; t2 < NB; ++t2)
+        acc = cfma(Uist[(NB - 1 - t) * NB + (NB - 1 - t2)], hd[t2 * NC + c], acc);
+      xs[t * NC + c] = acc;
     }
     __syncthreads();
 #pragma unroll
@@ -374,6 +399,95 @@ __global__ void __maxnreg__(REGS) band_solve_kernel(SolveArgsT<CT> a) {
   }
 }
 
+// ----------------------------------------------------------------------------------------------
+// Block transforms, computed once per factorisation (one warp per (panel, pole)):
+//  forward: the set H of a panel's NB steps (head rows j0..j0+NB-1, then for step jj its pivot
+//    row if it lies below the head and no earlier step named it; -1 = absent) and the 16x16
+//    matrix T such that the panel's interleaved swaps and eliminations restricted to H are
+//    H <- T H (T[:, m] = the steps applied to the unit vector of member m);
+//  backward: inv(U_block), the 8x8 inverse of U's diagonal block of the panel (rows and
+//    columns >= n are zero).
+// T and inv(U_block) are written in complex128 and, when T32/Ui32 are given, complex64.
+__global__ void block_transform_kernel(int64_t n, int64_t n_pad, int kl, int ldab, const cplx* AB,
+                                       const int* piv, const cplx* dinv, cplx* Tout, int* Hout,
+                                       cplx* Uiout, float2* T32, float2* Ui32) {
+  const int P = blockIdx.x, pole = blockIdx.y, lane = threadIdx.x;
+  const int kv = 2 * kl;
+  const int64_t npan = n_pad / NB;
+  const int64_t j0 = (int64_t)P * NB;
+  const int nvalid = (int)((n - j0) < NB ? (n - j0) : NB);
+  const cplx* A = AB + (int64_t)pole * n_pad * ldab;
+  const int* pv = piv + (int64_t)pole * n_pad;
+  const cplx* di = dinv + (int64_t)pole * n_pad;
+  int64_t pst[NB];
+#pragma unroll
+  for (int jj = 0; jj < NB; ++jj) pst[jj] = (jj < nvalid) ? pv[j0 + jj] : -1;
+  auto hidx = [&](int64_t r) -> int {
+    if (r >= j0 && r < j0 + NB) return (int)(r - j0);
+    for (int jj = 0; jj < nvalid; ++jj)
+      if (pst[jj] == r) return NB + jj;
+    return -1;
+  };
+  auto hrow = [&](int l) -> int64_t {
+    if (l < NB) return j0 + l;
+    if (l < 2 * NB) {
+      const int jj = l - NB;
+      if (jj < nvalid && pst[jj] >= j0 + NB && hidx(pst[jj]) == l) return pst[jj];
+    }
+    return -1;
+  };
+  const int64_t myrow = hrow(lane);
+  const int64_t base = (int64_t)pole * npan + P;
+  if (lane < 16) Hout[base * 16 + lane] = (int)myrow;
+  for (int m = 0; m < 16; ++m) {
+    const bool present = hrow(m) >= 0;
+    cplx val = make_double2((lane == m && present) ? 1.0 : 0.0, 0.0);
+    if (present) {
+      for (int jj = 0; jj < nvalid; ++jj) {
+        const int64_t j = j0 + jj;
+        const int b = hidx(pst[jj]);
+        const cplx x = make_double2(__shfl_sync(0xffffffffu, val.x, b), __shfl_sync(0xffffffffu, val.y, b));
+        const cplx va = make_double2(__shfl_sync(0xffffffffu, val.x, jj),
+                                     __shfl_sync(0xffffffffu, val.y, jj));
+        if (lane == jj) val = x;
+        else if (lane == b) val = va;
+        if (myrow > j && myrow <= j + kl) val = cfms(A[j * ldab + kv + (myrow - j)], x, val);
+      }
+    }
+    if (lane < 16) {
+      const cplx t = (myrow >= 0 && present) ? val : make_double2(0, 0);
+      Tout[base * 256 + lane * 16 + m] = t;
+      if (T32) T32[base * 256 + lane * 16 + m] = make_float2((float)t.x, (float)t.y);
+    }
+  }
+  // column b of inv(U_block) by back substitution: U(r, c) = A[c*ldab + kv + r - c], r <= c
+  if (lane < NB) {
+    const int b = lane;
+    cplx z[NB];
+#pragma unroll
+    for (int i = 0; i < NB; ++i) z[i] = make_double2(0, 0);
+    for (int i = b; i >= 0; --i) {
+      const int64_t r = j0 + i;
+      cplx acc = make_double2(i == b ? 1.0 : 0.0, 0.0);
+      for (int c = i + 1; c <= b; ++c)
+        if (c - i <= kv && j0 + c < n) acc = cfms(A[(j0 + c) * ldab + kv + (r - (j0 + c))], z[c], acc);
+      z[i] = (r < n) ? cmul(acc, di[r]) : make_double2(0, 0);
+    }
+    for (int i = 0; i < NB; ++i) {
+      const cplx t = z[i];
+      Uiout[base * 64 + i * NB + b] = t;
+      if (Ui32) Ui32[base * 64 + i * NB + b] = make_float2((float)t.x, (float)t.y);
+    }
+  }
+}
+
+void launch_block_transforms(int q, int64_t n, int64_t n_pad, int kl, int ldab, const cplx* AB,
+                             const int* piv, const cplx* dinv, cplx* T, int* H, cplx* Ui,
+                             float2* T32, float2* Ui32, cudaStream_t s) {
+  dim3 grid((unsigned)(n_pad / NB), (unsigned)q);
+  block_transform_kernel<<<grid, 32, 0, s>>>(n, n_pad, kl, ldab, AB, piv, dinv, T, H, Ui, T32, Ui32); ie_count_launch();
+}
+
 template <typename CT, int NC, int SPT, int REGS>
 static cudaError_t launch_solve_r(const SolveArgsT<CT>& a, int q, int threads, size_t smem,
                                   cudaStream_t s) {
@@ -404,8 +518,9 @@ static bool solve_shape(SolveArgsT<CT>& a, int* threads, int* spt, size_t* smem)
   *spt = slots > 576 ? 2 : 1;
   if (slots > 1152) return false;              // half bandwidth up to 572
   *threads = ((slots + *spt - 1) / *spt + 31) / 32 * 32;
-  const size_t stage_bytes =
-      (((size_t)NB * a.kvp * sizeof(CT) + NB * sizeof(CT)) + 127) & ~(size_t)127;
+  const size_t fwdb = (size_t)NB * a.klp * sizeof(CT) + 256 * sizeof(CT) + 16 * sizeof(int);
+  const size_t bwdb = (size_t)NB * a.kvp * sizeof(CT) + 64 * sizeof(CT);
+  const size_t stage_bytes = ((fwdb > bwdb ? fwdb : bwdb) + 127) & ~(size_t)127;
   const size_t fixed = 128 + (4 * 8 + 4 * NB * 8) * sizeof(CT) + 256;
   const size_t budget = 200 * 1024;
   int nstage = (int)((budget - fixed) / stage_bytes);
@@ -423,10 +538,11 @@ static int pick_nc(int q, int k, int sms, int ncmax) {
   return ncmax;
 }
 
-cudaError_t launch_band_solve(int q, int64_t n, int kl, int ldab, int64_t n_pad, const cplx* AB,
-                              const int* piv, const cplx* dinv, const cplx* d_weights,
-                              const cplx* RHS, int64_t ldr, int k, cplx* Xp, int64_t ldx,
-                              int64_t xstride, int* status, cudaStream_t s) {
+cudaError_t launch_band_solve(int q, int64_t n, int kl, int64_t n_pad, const cplx* L64,
+                              const cplx* U64, const int* piv, const cplx* dinv, const cplx* Tb, const int* Hb,
+                              const cplx* Ub, const cplx* d_weights, const cplx* RHS, int64_t ldr,
+                              int k, cplx* Xp, int64_t ldx, int64_t xstride, int* status,
+                              cudaStream_t s) {
   if (k <= 0) return cudaSuccess;
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
@@ -434,9 +550,10 @@ cudaError_t launch_band_solve(int q, int64_t n, int kl, int ldab, int64_t n_pad,
   SolveArgsT<cplx> a{};
   a.n = n; a.n_pad = n_pad; a.kl = kl; a.kv = 2 * kl; a.klp = kl; a.kvp = 2 * kl; a.k = k;
   a.mode = 0;
-  a.L = AB + a.kv + 1; a.U = AB; a.ldl = ldab; a.ldu = ldab;
-  a.lstride = n_pad * ldab; a.ustride = n_pad * ldab;
+  a.L = L64; a.U = U64; a.ldl = kl; a.ldu = 2 * kl;
+  a.lstride = n_pad * kl; a.ustride = n_pad * 2 * kl;
   a.piv = piv; a.dinv = dinv; a.weights = d_weights;
+  a.Tb = Tb; a.Hb = Hb; a.Ub = Ub;
   a.RHS = RHS; a.ldr = ldr; a.rstride = 0;
   a.Y = Xp; a.ldy = ldx; a.ystride = xstride;
   a.X = Xp; a.ldx = ldx; a.xstride = xstride;
@@ -461,7 +578,8 @@ cudaError_t launch_band_solve(int q, int64_t n, int kl, int ldab, int64_t n_pad,
 
 cudaError_t launch_band_solve32(int q, int64_t n, int kl, int64_t n_pad, const float2* L32,
                                 int64_t ldl, const float2* U32, int64_t ldu, const int* piv,
-                                const float2* dinv32, const cplx* d_weights, const float2* RHS,
+                                const float2* dinv32, const float2* T32, const int* Hb,
+                                const float2* Ui32, const cplx* d_weights, const float2* RHS,
                                 int64_t ldr, int64_t rstride, int k, float2* Y32, int64_t ldy,
                                 int64_t ystride, cplx* X, int64_t ldx, int64_t xstride,
                                 int accumulate, int* status, cudaStream_t s) {
@@ -476,6 +594,7 @@ cudaError_t launch_band_solve32(int q, int64_t n, int kl, int64_t n_pad, const f
   a.L = L32; a.U = U32; a.ldl = ldl; a.ldu = ldu;
   a.lstride = n_pad * ldl; a.ustride = n_pad * ldu;
   a.piv = piv; a.dinv = dinv32; a.weights = d_weights;
+  a.Tb = T32; a.Hb = Hb; a.Ub = Ui32;
   a.RHS = RHS; a.ldr = ldr; a.rstride = rstride;
   a.Y = Y32; a.ldy = ldy; a.ystride = ystride;
   a.X = X; a.ldx = ldx; a.xstride = xstride;

@@ -63,8 +63,8 @@ extern "C" ie_status ie_apply_G_static(ie_handle h, const ie_complex* d_V, int64
   // every element of BV and Xp read below is written first by this call
   launch_spmv(f.P, make_double2(0, 0), make_double2(1, 0), (const cplx*)d_V, ldv, nullptr, k, BV,
               f.n, s);
-  e = launch_band_solve(f.q, f.n, f.kl, f.ldab, f.n_pad, f.AB, f.piv, f.dinv, f.weights, BV, f.n,
-                        k, Xp, f.n, f.n * (int64_t)k, f.status, s);
+  e = launch_band_solve(f.q, f.n, f.kl, f.n_pad, f.L64, f.U64, f.piv, f.dinv, f.Tb, f.Hb, f.Ub,
+                        f.weights, BV, f.n, k, Xp, f.n, f.n * (int64_t)k, f.status, s);
   if (e != cudaSuccess) return IE_ERR_CUDA;
   launch_pole_sum(f.q, f.n, k, Xp, f.n, f.n * (int64_t)k, (cplx*)d_GV, ldgv, s);
   if (cudaGetLastError() != cudaSuccess) return IE_ERR_CUDA;
