@@ -46,6 +46,9 @@ def parse():
     ap.add_argument("--solve", type=int, default=1,
                     help="1: also time one full ie_create + ie_solve per driver (time to all "
                          "eigenpairs in D at residual 1e-10), outside the throughput steps")
+    ap.add_argument("--mixed", type=int, default=1,
+                    help="1 (with --precision 0): also report the mixed-precision path on the same "
+                         "workload (throughput and time to all eigenpairs at the same residual)")
     ap.add_argument("--precision", type=int, default=0, choices=[0, 1],
                     help="0: complex128 factors and solves; 1: complex64 factors, FP32 solves, "
                          "FP64 refinement")
@@ -215,14 +218,11 @@ def run_native(args):
     value = cols / (t_ms / 1e3)
     gpu_launches = int(sB["kernel_launches"] - sA["kernel_launches"])   # counted by libie
 
-    solves = None
-    if args.solve and rank == 0:
-        solves = {}
-        ie.ie_destroy(h)
-        h = None
+    def time_solves(precision):
+        out = {}
         ref = np.array(w["eig_in_disk_re"]) + 1j * np.array(w["eig_in_disk_im"])
         for drv in (1, 2):
-            o = ie.ie_opts_default(k=k, m_max=150, precision=args.precision, driver=drv)
+            o = ie.ie_opts_default(k=k, m_max=150, precision=precision, driver=drv)
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             st0, hs = ie.ie_create(n, pen.offsets, A_d, B_d, w["center"], w["radius"], p, q, o,
@@ -235,13 +235,20 @@ def run_native(args):
             got = lam[:nf]
             err = (float(np.max(np.min(np.abs(got[:, None] - ref[None, :]), axis=1) / np.abs(got)))
                    if nf else None)
-            solves[f"alg{drv}"] = {
+            out[f"alg{drv}"] = {
                 "seconds": tt, "status": ie.ie_status_str(st1), "n_found": nf,
                 "n_in_disk_reference": int(len(ref)), "max_rho": float(np.max(rho[:nf])) if nf else None,
                 "max_rel_err_vs_reference": err, "outer_iters": sst["outer_iters"],
                 "p_final": sst["p_final"], "factor_ms": sst["t_factor_ms"],
                 "filter_ms": sst["t_filter_ms"], "hsrr_ms": sst["t_hsrr_ms"]}
             ie.ie_destroy(hs)
+        return out
+
+    solves = None
+    if args.solve and rank == 0:
+        ie.ie_destroy(h)
+        h = None
+        solves = time_solves(args.precision)
         st, h = ie.ie_create(n, pen.offsets, A_d, B_d, w["center"], w["radius"], p, q, opts, stream)
 
     e2e = None
@@ -261,6 +268,39 @@ def run_native(args):
                "h2d_bytes_per_step": 2 * nb, "d2h_bytes_per_step": 2 * nb + k * 16 * 3,
                "api": "ie_filter_apply + ie_hsrr on pinned host buffers"}
     ie.ie_destroy(h)
+
+    mixed = None
+    if args.mixed and args.precision == 0 and rank == 0:
+        # the mixed-precision path on the same workload: throughput over the same steps (one
+        # warm-up step, which also lets the launch-shape tuner settle) and time to all
+        # eigenpairs at the same 1e-10 residual
+        om = ie.ie_opts_default(k=k, m_max=150, precision=1)
+        stm, h = ie.ie_create(n, pen.offsets, A_d, B_d, w["center"], w["radius"], p, q, om, stream)
+        step(Yd, Ud, Xd)
+        torch.cuda.synchronize()
+        _, mA = ie.ie_get_stats(h)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            step(Yd, Ud, Xd)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        tm = e0.elapsed_time(e1)
+        _, mB = ie.ie_get_stats(h)
+        ins = np.abs(last["lam"] - w["center"]) < w["radius"]
+        ml = mB["solve32_launches"] - mA["solve32_launches"]
+        mms = mB["t_solve32_ms"] - mA["t_solve32_ms"]
+        mfl = mB["solve32_flops"] - mA["solve32_flops"]
+        ie.ie_destroy(h)
+        mixed = {"dtype": "c64 factors and solves, f64 refinement (2 steps), f64 Krylov/HSRR",
+                 "value": k * args.steps / (tm / 1e3), "unit": "filtered columns/s",
+                 "ms_per_step": tm / args.steps,
+                 "ritz_in_disk_rho_max": float(np.max(last["rho"][ins])) if ins.any() else None,
+                 "band_solve_c64": {"launches": ml, "avg_launch_ms": mms / ml if ml else None,
+                                    "achieved_tflops": mfl / (mms / 1e3) / 1e12 if mms > 0 else None,
+                                    "peak_tflops": FP32_PEAK_TFLOPS},
+                 "time_to_all_eigenpairs": time_solves(1) if args.solve else None}
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -303,6 +343,7 @@ def run_native(args):
                          "share_of_step": solve_ms / t_ms if t_ms > 0 else None},
             "gpu_launches": gpu_launches,
             "time_to_all_eigenpairs": solves,
+            "mixed_precision": mixed,
             "e2e": e2e,
             "clocks": clk.summary(),
             "cpu_baseline": cpu,

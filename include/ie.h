@@ -175,7 +175,9 @@ ie_status ie_get_coeffs(ie_handle h, ie_complex* h_poles, ie_complex* h_weights,
                         ie_complex* h_shifts, ie_complex* h_cweights, int32_t* n_shift,
                         double* odd_coef);
 
-/* ie_get_factor: copies pole i's band LU (LAPACK zgbtrf layout: column j holds
+/* ie_get_factor (complex128 handles only; IE_ERR_ARG for precision = 1, whose
+ * complex128 factors are released after their complex64 copy is made):
+ * copies pole i's band LU (LAPACK zgbtrf layout: column j holds
  * rows j-kv..j+kl at offsets 0..ldab-1 with kv = 2*kl, ldab = 3*kl + 1; U in rows
  * 0..kv, the multipliers of L below) and its 1-based pivot vector (LAPACK ipiv
  * convention) into host arrays h_ab (ldab * n) and h_ipiv (n). *kl, *ldab set. */
@@ -194,7 +196,8 @@ ie_status ie_get_stats(ie_handle h, ie_stats* out);
  * and the q per-pole solve buffers) lives in one file-scope device array of
  * IE_STATIC_SCRATCH_BYTES bytes, which every GPU that loads the library keeps until the
  * process exits. Limit: (q + 1) * n * k * 16 <= IE_STATIC_SCRATCH_BYTES, else
- * IE_ERR_SCRATCH_LIMIT (nothing is launched). d_V, d_GV: device pointers, n x k, ld >= n;
+ * IE_ERR_SCRATCH_LIMIT (nothing is launched). Complex128 handles only (precision = 0;
+ * IE_ERR_ARG otherwise). d_V, d_GV: device pointers, n x k, ld >= n;
  * the current device must be the handle's. The first call on a device looks up the array's
  * device address (cudaGetSymbolAddress) once for that device; make that first call before
  * any stream capture. All calls in the process share the one array: calls whose work

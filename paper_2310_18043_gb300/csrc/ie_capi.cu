@@ -406,10 +406,12 @@ extern "C" ie_status ie_create(const ie_pencil* pen, ie_complex center, double r
   if (st[ST_TIMEOUT]) return fail(IE_ERR_TIMEOUT);
   {
     const size_t np = (size_t)(h->n_pad / 8);
-    if (h->alloc(&h->L64, (size_t)q * h->n_pad * kl) != cudaSuccess ||
-        h->alloc(&h->U64, (size_t)q * h->n_pad * h->kv) != cudaSuccess)
-      return fail(IE_ERR_OOM);
-    launch_factors_split64(q, h->n_pad, kl, h->ldab, h->AB, h->L64, h->U64, s);
+    if (opts.precision == 0) {   // the complex64 path has its own split copy
+      if (h->alloc(&h->L64, (size_t)q * h->n_pad * kl) != cudaSuccess ||
+          h->alloc(&h->U64, (size_t)q * h->n_pad * h->kv) != cudaSuccess)
+        return fail(IE_ERR_OOM);
+      launch_factors_split64(q, h->n_pad, kl, h->ldab, h->AB, h->L64, h->U64, s);
+    }
     if (h->alloc(&h->Tb, (size_t)q * np * 256) != cudaSuccess ||
         h->alloc(&h->Hb, (size_t)q * np * 16) != cudaSuccess ||
         h->alloc(&h->Uinvb, (size_t)q * np * 64) != cudaSuccess)
@@ -436,6 +438,9 @@ extern "C" ie_status ie_create(const ie_pencil* pen, ie_complex center, double r
     launch_factors_to_c64(q, h->n_pad, kl, h->ldab, h->klp, h->AB, h->dinv, h->L32, h->U32,
                           h->dinv32, s);
     if (cudaStreamSynchronize(s) != cudaSuccess) return fail(IE_ERR_CUDA);
+    // the complex128 band factors are no longer used by this handle
+    h->release(h->AB);
+    h->AB = nullptr;
   }
   if (cudaGetLastError() != cudaSuccess) return fail(IE_ERR_CUDA);
   *out = h;
@@ -936,7 +941,7 @@ extern "C" ie_status ie_get_coeffs(ie_handle h, ie_complex* h_poles, ie_complex*
 
 extern "C" ie_status ie_get_factor(ie_handle h, int32_t pole, ie_complex* h_ab, int32_t* h_ipiv,
                                    int32_t* kl, int32_t* ldab) {
-  if (!h || pole < 0 || pole >= h->q) return IE_ERR_ARG;
+  if (!h || pole < 0 || pole >= h->q || !h->AB) return IE_ERR_ARG;
   if (kl) *kl = h->kl;
   if (ldab) *ldab = h->ldab;
   if (h_ab)

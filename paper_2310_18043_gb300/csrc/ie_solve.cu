@@ -14,6 +14,12 @@
 // Factor columns (L parts forward, U parts backward, with pivots / 1/u_jj) are staged NB at a
 // time into a shared ring by cp.async.bulk (TMA bulk copies) with mbarrier completion; every
 // wait is bounded.
+#include <cstdlib>
+#include <map>
+#include <mutex>
+#include <tuple>
+#include <vector>
+
 #include "ie_internal.cuh"
 
 namespace {
@@ -63,15 +69,6 @@ __device__ __forceinline__ float2 cfms(float2 a, float2 b, float2 c) {
 }
 __device__ __forceinline__ float2 cfma(float2 a, float2 b, float2 c) {
   return make_float2(fmaf(a.x, b.x, fmaf(-a.y, b.y, c.x)), fmaf(a.x, b.y, fmaf(a.y, b.x, c.y)));
-}
-__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
-  return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
-}
-__device__ __forceinline__ double2 shfl_c(double2 v, int src) {
-  return make_double2(__shfl_sync(0xffffffffu, v.x, src), __shfl_sync(0xffffffffu, v.y, src));
-}
-__device__ __forceinline__ float2 shfl_c(float2 v, int src) {
-  return make_float2(__shfl_sync(0xffffffffu, v.x, src), __shfl_sync(0xffffffffu, v.y, src));
 }
 __device__ __forceinline__ double2 to_d(double2 v) { return v; }
 __device__ __forceinline__ double2 to_d(float2 v) { return make_double2(v.x, v.y); }
@@ -143,6 +140,15 @@ __global__ void __maxnreg__(REGS) band_solve_kernel(SolveArgsT<CT> a) {
   const size_t bwd_bytes = bwd_cols_bytes + 64 * sizeof(CT);
   const size_t stage_bytes = ((fwd_bytes > bwd_bytes ? fwd_bytes : bwd_bytes) + 127) & ~(size_t)127;
   __shared__ int s_fail;
+  {
+    // the staged ring must lie inside the dynamic allocation; refuse to run otherwise
+    unsigned dsz;
+    asm("mov.u32 %0, %%dynamic_smem_size;" : "=r"(dsz));
+    if ((size_t)(stage0 - sm_raw) + (size_t)a.nstage * stage_bytes > (size_t)dsz) {
+      if (tid == 0) atomicExch(a.status + ST_TIMEOUT, 1);
+      return;
+    }
+  }
 
   if (tid == 0) {
     s_fail = 0;
@@ -198,17 +204,25 @@ __global__ void __maxnreg__(REGS) band_solve_kernel(SolveArgsT<CT> a) {
     const int* Hst = (const int*)(stage0 + (size_t)st * stage_bytes + fwd_cols_bytes + 256 * sizeof(CT));
     const int64_t j0 = P * NB;
     const int nvalid = (int)((n - j0) < NB ? (n - j0) : NB);
-    // (A) gather the members' values
+    // (A) gather the members' values; a slot's member index: head rows by arithmetic, pivot
+    // members by comparing with H's last 8 entries
+    int mem[SPT];
 #pragma unroll
     for (int u = 0; u < SPT; ++u) {
       const int s = tid + u * T;
+      mem[u] = -1;
       if (s >= Sf) continue;
       const int64_t r = frow[u];
-      for (int i = 0; i < 16; ++i)
-        if (Hst[i] == r) {
+      if (r >= j0 && r < j0 + NB) {
+        mem[u] = (int)(r - j0);
+      } else {
 #pragma unroll
-          for (int c = 0; c < NC; ++c) hv[i * NC + c] = v[u][c];
-        }
+        for (int i = NB; i < 16; ++i)
+          if (Hst[i] == r) mem[u] = i;
+      }
+      if (mem[u] >= 0)
+#pragma unroll
+        for (int c = 0; c < NC; ++c) hv[mem[u] * NC + c] = v[u][c];
     }
     __syncthreads();
     // (B) H <- T H
@@ -228,9 +242,7 @@ __global__ void __maxnreg__(REGS) band_solve_kernel(SolveArgsT<CT> a) {
       const int s = tid + u * T;
       if (s >= Sf) continue;
       const int64_t r = frow[u];
-      int i = -1;
-      for (int m = 0; m < 16; ++m)
-        if (Hst[m] == r) i = m;
+      const int i = mem[u];
       if (i >= 0 && i < NB) {
         if (r < n)
 #pragma unroll
@@ -291,6 +303,9 @@ __global__ void __maxnreg__(REGS) band_solve_kernel(SolveArgsT<CT> a) {
   };
   const int Sb = kv + NB;
   int64_t row[SPT];
+  // mode 2 (complex64 path only): the FP64 value the row's result is added to, loaded on entry
+  constexpr bool kAcc = sizeof(CT) == sizeof(float2);
+  cplx xold[kAcc ? SPT : 1][kAcc ? NC : 1];
   if (tid == 0)
     for (int st = 0; st < a.nstage && st < npanel; ++st) issue_bwd(st, st);
   {
@@ -306,6 +321,12 @@ __global__ void __maxnreg__(REGS) band_solve_kernel(SolveArgsT<CT> a) {
         const int64_t rn = r - Sb;
         nxt[u][c] = (s < Sb && rn >= 0 && rn < n && c < ncol) ? Yo[(int64_t)(c0 + c) * a.ldy + rn]
                                                              : zero;
+      }
+      if constexpr (kAcc) {
+#pragma unroll
+        for (int c = 0; c < NC; ++c)
+          xold[u][c] = (a.mode == 2 && s < Sb && r >= 0 && r < n && c < ncol)
+                           ? Xo[(int64_t)(c0 + c) * a.ldx + r] : make_double2(0, 0);
       }
       if (s < Sb && r > j0 - NB)
 #pragma unroll
@@ -354,9 +375,8 @@ __global__ void __maxnreg__(REGS) band_solve_kernel(SolveArgsT<CT> a) {
             }
             if (a.mode == 1) {
               Xo[(int64_t)(c0 + c) * a.ldx + r] = to_d(xv);
-            } else {
-              cplx* p = Xo + (int64_t)(c0 + c) * a.ldx + r;
-              *p = cadd(*p, to_d(xv));
+            } else if constexpr (kAcc) {
+              Xo[(int64_t)(c0 + c) * a.ldx + r] = cadd(xold[u][c], to_d(xv));
             }
           }
         }
@@ -367,6 +387,9 @@ __global__ void __maxnreg__(REGS) band_solve_kernel(SolveArgsT<CT> a) {
           v[u][c] = nxt[u][c];
           const int64_t rn = r - Sb;
           nxt[u][c] = (rn >= 0 && c < ncol) ? Yo[(int64_t)(c0 + c) * a.ldy + rn] : zero;
+          if constexpr (kAcc)
+            xold[u][c] = (a.mode == 2 && r >= 0 && c < ncol) ? Xo[(int64_t)(c0 + c) * a.ldx + r]
+                                                             : make_double2(0, 0);
         }
         // a refilled row lies below every column of this block's band: no update; with
         // kv < NB it can already be a head row of the next block
@@ -510,25 +533,46 @@ static cudaError_t launch_solve_t(const SolveArgsT<CT>& a, int q, int threads, s
   return launch_solve_r<CT, NC, SPT, 96>(a, q, threads, smem, s);
 }
 
-// threads, stages and shared memory for a solve with element type CT; returns false if the
-// band is too wide for one CTA
+// One launch shape: NC right-hand sides per CTA, SPT window slots per thread, at most
+// `stages` staged panels.
+struct SolveCfg {
+  int nc, spt, stages;
+};
+
+// threads, stages and dynamic shared memory of a shape; false if the shape cannot hold the band
 template <typename CT>
-static bool solve_shape(SolveArgsT<CT>& a, int* threads, int* spt, size_t* smem) {
-  const int slots = a.kv + NB;                // backward window (larger than kl + NB)
-  *spt = slots > 576 ? 2 : 1;
-  if (slots > 1152) return false;              // half bandwidth up to 572
-  *threads = ((slots + *spt - 1) / *spt + 31) / 32 * 32;
+static bool shape_for(SolveArgsT<CT>& a, const SolveCfg& c, int* threads, size_t* smem) {
+  const int slots = a.kv + NB;                  // backward window (larger than kl + NB)
+  if ((slots + c.spt - 1) / c.spt > 576) return false;
+  *threads = ((slots + c.spt - 1) / c.spt + 31) / 32 * 32;
   const size_t fwdb = (size_t)NB * a.klp * sizeof(CT) + 256 * sizeof(CT) + 16 * sizeof(int);
   const size_t bwdb = (size_t)NB * a.kvp * sizeof(CT) + 64 * sizeof(CT);
   const size_t stage_bytes = ((fwdb > bwdb ? fwdb : bwdb) + 127) & ~(size_t)127;
-  const size_t fixed = 128 + (4 * 8 + 4 * NB * 8) * sizeof(CT) + 256;
+  // mbarriers, then bc [4][NC], hd and xs [NB][NC], hv and hv2 [16][NC], alignment slack
+  const size_t fixed = 128 + (size_t)(4 + 2 * NB + 32) * c.nc * sizeof(CT) + 256;
   const size_t budget = 200 * 1024;
+  if (fixed + 2 * stage_bytes > budget) return false;
   int nstage = (int)((budget - fixed) / stage_bytes);
-  if (nstage > 6) nstage = 6;
-  if (nstage < 2) return false;
+  if (nstage > c.stages) nstage = c.stages;
   a.nstage = nstage;
   *smem = fixed + (size_t)nstage * stage_bytes;
   return true;
+}
+
+template <typename CT>
+static cudaError_t launch_cfg(SolveArgsT<CT> a, int q, const SolveCfg& c, cudaStream_t s) {
+  int threads;
+  size_t smem;
+  if (!shape_for(a, c, &threads, &smem)) return cudaErrorInvalidValue;
+#define IE_SOLVE_CASE(NC_, SPT_) \
+  if (c.nc == NC_ && c.spt == SPT_) return launch_solve_t<CT, NC_, SPT_>(a, q, threads, smem, s);
+  IE_SOLVE_CASE(1, 1) IE_SOLVE_CASE(2, 1) IE_SOLVE_CASE(4, 1)
+  IE_SOLVE_CASE(1, 2) IE_SOLVE_CASE(2, 2) IE_SOLVE_CASE(4, 2)
+  if constexpr (sizeof(CT) == sizeof(float2)) {
+    IE_SOLVE_CASE(8, 1) IE_SOLVE_CASE(8, 2)
+  }
+#undef IE_SOLVE_CASE
+  return cudaErrorInvalidValue;
 }
 
 static int pick_nc(int q, int k, int sms, int ncmax) {
@@ -538,15 +582,117 @@ static int pick_nc(int q, int k, int sms, int ncmax) {
   return ncmax;
 }
 
+// Online autotuner of the launch shape. For each (element type, band, poles, block width
+// rounded up to a power of two) the first launches each use a different candidate shape,
+// timed with CUDA events; once all are timed, the fastest is used. Every candidate does the
+// same arithmetic per column (results are identical), so tuning costs no extra work.
+// IE_SOLVE_TUNE=0 in the environment disables it (the default shape is used).
+namespace {
+struct TuneKey {
+  int esize, kl, q, kb;
+  bool operator<(const TuneKey& o) const {
+    return std::tie(esize, kl, q, kb) < std::tie(o.esize, o.kl, o.q, o.kb);
+  }
+};
+struct TuneState {
+  std::vector<SolveCfg> cand;
+  std::vector<cudaEvent_t> e0, e1;
+  std::vector<float> ms;   // < 0: pending; +inf: shape not launchable
+  int next = 0, best = -1;
+};
+std::mutex g_tune_mu;
+std::map<TuneKey, TuneState> g_tune;
+bool tune_enabled() {
+  static const bool on = [] {
+    const char* e = getenv("IE_SOLVE_TUNE");
+    return !(e && e[0] == '0');
+  }();
+  return on;
+}
+}  // namespace
+
+template <typename CT>
+static cudaError_t launch_tuned(const SolveArgsT<CT>& a, int q, cudaStream_t s) {
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const bool fp32 = sizeof(CT) == sizeof(float2);
+  const int spt0 = (a.kv + NB > 576) ? 2 : 1;
+  const SolveCfg dflt{pick_nc(q, a.k, sms, fp32 ? 8 : 4), spt0, 6};
+  if (!tune_enabled()) return launch_cfg(a, q, dflt, s);
+  int kb = 1;
+  while (kb < a.k) kb *= 2;
+  const TuneKey key{(int)sizeof(CT), a.kl, q, kb};
+  SolveCfg use = dflt;
+  int slot = -1;
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    TuneState& T = g_tune[key];
+    if (T.cand.empty()) {
+      std::vector<SolveCfg> c = {dflt, {2, 2, 3}, {4, 2, 3}, {2, 1, 3}, {1, 2, 3}, {4, 1, 3}};
+      if (fp32) {
+        c.push_back({8, 1, 3});
+        c.push_back({8, 2, 2});
+        c.push_back({2, 2, 2});
+      }
+      for (const SolveCfg& x : c) {
+        if (x.spt < spt0) continue;
+        bool dup = false;
+        for (const SolveCfg& y : T.cand) dup |= (y.nc == x.nc && y.spt == x.spt && y.stages == x.stages);
+        if (!dup) T.cand.push_back(x);
+      }
+      T.e0.resize(T.cand.size());
+      T.e1.resize(T.cand.size());
+      for (size_t i = 0; i < T.cand.size(); ++i) {
+        cudaEventCreate(&T.e0[i]);
+        cudaEventCreate(&T.e1[i]);
+      }
+      T.ms.assign(T.cand.size(), -1.0f);
+    }
+    if (T.best >= 0) {
+      use = T.cand[T.best];
+    } else {
+      bool all = T.next == (int)T.cand.size();
+      for (int i = 0; i < T.next; ++i) {
+        if (T.ms[i] >= 0.0f) continue;
+        if (cudaEventQuery(T.e1[i]) == cudaSuccess) cudaEventElapsedTime(&T.ms[i], T.e0[i], T.e1[i]);
+        else { cudaGetLastError(); all = false; }
+      }
+      if (all) {
+        int b = 0;
+        for (int i = 1; i < (int)T.cand.size(); ++i)
+          if (T.ms[i] < T.ms[b]) b = i;
+        T.best = b;
+        use = T.cand[b];
+      } else if (T.next < (int)T.cand.size()) {
+        slot = T.next++;
+        use = T.cand[slot];
+      }
+    }
+    if (slot >= 0) cudaEventRecord(T.e0[slot], s);
+  }
+  cudaError_t e = launch_cfg(a, q, use, s);
+  if (slot >= 0) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    TuneState& T = g_tune[key];
+    if (e == cudaSuccess) {
+      cudaEventRecord(T.e1[slot], s);
+    } else {   // shape not launchable here: never pick it, compute this call with the default
+      cudaGetLastError();
+      T.ms[slot] = 3.0e38f;
+      cudaEventRecord(T.e1[slot], s);
+      e = launch_cfg(a, q, dflt, s);
+    }
+  }
+  return e;
+}
+
 cudaError_t launch_band_solve(int q, int64_t n, int kl, int64_t n_pad, const cplx* L64,
                               const cplx* U64, const int* piv, const cplx* dinv, const cplx* Tb, const int* Hb,
                               const cplx* Ub, const cplx* d_weights, const cplx* RHS, int64_t ldr,
                               int k, cplx* Xp, int64_t ldx, int64_t xstride, int* status,
                               cudaStream_t s) {
   if (k <= 0) return cudaSuccess;
-  int dev = 0, sms = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   SolveArgsT<cplx> a{};
   a.n = n; a.n_pad = n_pad; a.kl = kl; a.kv = 2 * kl; a.klp = kl; a.kvp = 2 * kl; a.k = k;
   a.mode = 0;
@@ -558,22 +704,7 @@ cudaError_t launch_band_solve(int q, int64_t n, int kl, int64_t n_pad, const cpl
   a.Y = Xp; a.ldy = ldx; a.ystride = xstride;
   a.X = Xp; a.ldx = ldx; a.xstride = xstride;
   a.status = status;
-  int threads, spt;
-  size_t smem;
-  if (!solve_shape(a, &threads, &spt, &smem)) return cudaErrorInvalidValue;
-  int NC = pick_nc(q, k, sms, 4);
-  if (NC == 8) NC = 4;
-  if (spt == 1) {
-    switch (NC) {
-      case 1: return launch_solve_t<cplx, 1, 1>(a, q, threads, smem, s);
-      case 2: return launch_solve_t<cplx, 2, 1>(a, q, threads, smem, s);
-      default: return launch_solve_t<cplx, 4, 1>(a, q, threads, smem, s);
-    }
-  }
-  switch (NC) {
-    case 1: return launch_solve_t<cplx, 1, 2>(a, q, threads, smem, s);
-    default: return launch_solve_t<cplx, 2, 2>(a, q, threads, smem, s);
-  }
+  return launch_tuned(a, q, s);
 }
 
 cudaError_t launch_band_solve32(int q, int64_t n, int kl, int64_t n_pad, const float2* L32,
@@ -584,9 +715,6 @@ cudaError_t launch_band_solve32(int q, int64_t n, int kl, int64_t n_pad, const f
                                 int64_t ystride, cplx* X, int64_t ldx, int64_t xstride,
                                 int accumulate, int* status, cudaStream_t s) {
   if (k <= 0) return cudaSuccess;
-  int dev = 0, sms = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   SolveArgsT<float2> a{};
   a.n = n; a.n_pad = n_pad; a.kl = kl; a.kv = 2 * kl;
   a.klp = (int)ldl; a.kvp = (int)ldu;   // padded column lengths = column strides
@@ -599,22 +727,5 @@ cudaError_t launch_band_solve32(int q, int64_t n, int kl, int64_t n_pad, const f
   a.Y = Y32; a.ldy = ldy; a.ystride = ystride;
   a.X = X; a.ldx = ldx; a.xstride = xstride;
   a.status = status;
-  int threads, spt;
-  size_t smem;
-  if (!solve_shape(a, &threads, &spt, &smem)) return cudaErrorInvalidValue;
-  // latency-bound in FP32: more columns per CTA amortise each row's barrier
-  const int NC = pick_nc(q, k, sms, 8);
-  if (spt == 1) {
-    switch (NC) {
-      case 1: return launch_solve_t<float2, 1, 1>(a, q, threads, smem, s);
-      case 2: return launch_solve_t<float2, 2, 1>(a, q, threads, smem, s);
-      case 4: return launch_solve_t<float2, 4, 1>(a, q, threads, smem, s);
-      default: return launch_solve_t<float2, 8, 1>(a, q, threads, smem, s);
-    }
-  }
-  switch (NC) {
-    case 1: return launch_solve_t<float2, 1, 2>(a, q, threads, smem, s);
-    case 2: return launch_solve_t<float2, 2, 2>(a, q, threads, smem, s);
-    default: return launch_solve_t<float2, 4, 2>(a, q, threads, smem, s);
-  }
+  return launch_tuned(a, q, s);
 }

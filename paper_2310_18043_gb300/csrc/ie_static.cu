@@ -47,6 +47,7 @@ extern "C" ie_status ie_apply_G_static(ie_handle h, const ie_complex* d_V, int64
   IeFactorsView f;
   if (!ie_internal_factors(h, &f) || !d_V || !d_GV || k < 1 || ldv < f.n || ldgv < f.n)
     return IE_ERR_ARG;
+  if (!f.L64 || !f.U64) return IE_ERR_ARG;   // complex128 handles only (precision = 0)
   int cur = -1;
   if (cudaGetDevice(&cur) != cudaSuccess || cur != f.dev) return IE_ERR_ARG;
   if (!on_device(d_V) || !on_device(d_GV)) return IE_ERR_ARG;

@@ -38,6 +38,8 @@ SPECS = {
     "p1_m160": dict(m=160, seed=3, p=8, q=8, k=64, n_in=30, driver=1),
     # at scale: m=256 (n=65,536, band 256), q=p=8, k=64, ~40 eigenvalues, both drivers
     "c2_m256": dict(m=256, seed=0, p=8, q=8, k=64, n_in=40, driver=1),
+    # precision: m=512 (n=262,144, band 512), q=p=8, k=96, mixed-precision solves
+    "c4_m512": dict(m=512, seed=0, p=8, q=8, k=96, n_in=60, driver=2, precision=1),
 }
 
 

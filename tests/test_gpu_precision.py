@@ -76,3 +76,16 @@ def test_mixed_solve_matches_golden(ie, name, driver):
         assert np.all(rho[:nf] <= 1e-10)
     finally:
         c.close()
+
+
+def test_mixed_handle_has_no_complex128_factors(ie):
+    """A precision = 1 handle releases its complex128 factors: the entry points that read
+    them refuse it instead of touching released memory."""
+    c = mixed(ie, "c1_m24")
+    try:
+        st, ab, ipiv, kl = ie.ie_get_factor(c.h, 0, c.n, 3 * c.pen.half_bw + 1)
+        assert st == ie.IE_ERR_ARG
+        V = dblock(ie_inputs.random_block(c.n, 2, seed=1))
+        assert ie.ie_apply_G_static(c.h, V, dzeros(c.n, 2)) == ie.IE_ERR_ARG
+    finally:
+        c.close()

@@ -82,3 +82,26 @@ def test_c2_solve_matches_reference_eigenvalues(ie, driver):
         assert np.all(rho2 <= 1e-10)
     finally:
         c.close()
+
+
+def test_c4_mixed_precision_solve(ie):
+    """The precision configuration: m = 512 (n = 262,144, band 512), q = p = 8, k = 96,
+    complex64 factors and FP32 band solves with FP64 refinement, Alg. 2. All 60 reference
+    eigenvalues (shift-invert Arnoldi) to 1e-10 relative, rho <= 1e-10. The disk boundary
+    is tight here (0.27% relative gap), and stopping at rho < 1e-10 left one eigenvalue at
+    2.7e-10 relative. The stop tolerance tau is a user parameter; 1e-12 gives the margin the
+    1e-10 eigenvalue bar needs."""
+    c = Case(ie, "c4_m512", driver=2, m_max=150, precision=1, tau=1e-12)
+    try:
+        k = c.w["k"]
+        Y0 = ie_inputs.orthonormal_random_block(c.n, k, seed=c.w["seed"])
+        Xd = dzeros(c.n, k)
+        st, lam, rho, e, nf, stats = ie.ie_solve(c.h, dblock(Y0), Xd, k)
+        assert st == ie.IE_OK, ie.ie_status_str(st)
+        ref = golden_eigs(c.w)
+        assert nf == len(ref) == 60
+        match_eigs(lam[:nf], ref)
+        assert np.all(rho[:nf] <= 1e-10)
+        assert stats["solve32_launches"] > 0 and stats["solve_launches"] == 0
+    finally:
+        c.close()
