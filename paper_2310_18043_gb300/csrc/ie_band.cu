@@ -1,5 +1,5 @@
 // Band kernels of the inner operator G (Sec. 3.2, Eq. linearsolve2):
-//   assembly of K_i = p_i B - A (Alg. 1 line 3) into LAPACK band storage,
+//   assembly of K_i = p_i B - A (Alg. 1) into LAPACK band storage,
 //   batched band LU with partial pivoting over all q poles in one cooperative launch,
 //   the DIA SpMV with A and B, the pole sums, and the complex64 factor copy and FP64
 //   residuals of the mixed-precision path (the triangular solves are in ie_solve.cu).
@@ -155,7 +155,7 @@ __device__ bool pole_barrier(unsigned* cnt, unsigned* gen, unsigned nb, unsigned
   return s_ok != 0;
 }
 
-__global__ void __launch_bounds__(256) band_lu_kernel(int64_t n, int kl, int ldab, int64_t n_pad,
+__global__ void __launch_bounds__(512) band_lu_kernel(int64_t n, int kl, int ldab, int64_t n_pad,
                                                       cplx* AB, int* piv, cplx* dinv,
                                                       unsigned* bar, int* status, int P,
                                                       int nown_max) {
@@ -238,14 +238,30 @@ __global__ void __launch_bounds__(256) band_lu_kernel(int64_t n, int kl, int lda
     }
     __syncthreads();
     if (nown > 0 && nrows > 0) {
+      // rank-1 update, LU_BATCH independent loads in flight per thread before the stores
+      constexpr int LU_BATCH = 8;
       const int tot = nrows * nown;
-      for (int it = tid; it < tot; it += T) {
-        const int idx = it / nrows;
-        const int t = 1 + (it - idx * nrows);
-        const int64_t l = l0 + (int64_t)idx * P;
-        cplx* cl = A + l * ldab + kv - (l - j);
-        cplx v = (t == tp) ? arow[idx] : __ldcg(cl + t);
-        cl[t] = cfms(mult[t], urow[idx], v);
+      for (int it0 = tid; it0 < tot; it0 += T * LU_BATCH) {
+        cplx val[LU_BATCH];
+        cplx* dst[LU_BATCH];
+        int tt[LU_BATCH], ii[LU_BATCH];
+#pragma unroll
+        for (int u = 0; u < LU_BATCH; ++u) {
+          const int it = it0 + u * T;
+          ii[u] = -1;
+          if (it < tot) {
+            const int idx = it / nrows;
+            const int t = 1 + (it - idx * nrows);
+            const int64_t l = l0 + (int64_t)idx * P;
+            dst[u] = A + l * ldab + kv - (l - j) + t;
+            tt[u] = t;
+            ii[u] = idx;
+            val[u] = (t == tp) ? arow[idx] : __ldcg(dst[u]);
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < LU_BATCH; ++u)
+          if (ii[u] >= 0) *dst[u] = cfms(mult[tt[u]], urow[ii[u]], val[u]);
       }
     }
     for (int idx = tid; idx < nown; idx += T) {
@@ -283,7 +299,7 @@ cudaError_t launch_band_lu(int q, int64_t n, int kl, int ldab, int64_t n_pad, cp
   size_t smem = (size_t)(2 * (kl + 1) + 2 * nown_max) * sizeof(cplx);
   if (smem > 48 * 1024)
     cudaFuncSetAttribute(band_lu_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, band_lu_kernel, 256, smem);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, band_lu_kernel, 512, smem);
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
   while ((int64_t)P * q > (int64_t)per_sm * sms && P > 1) {
     --P;
@@ -294,7 +310,7 @@ cudaError_t launch_band_lu(int q, int64_t n, int kl, int ldab, int64_t n_pad, cp
   cudaMemsetAsync(bar, 0, sizeof(unsigned) * 2 * q, s);
   void* args[] = {&n, &kl, &ldab, &n_pad, &AB, &piv, &dinv, &bar, &status, &P, &nown_max};
   ie_count_launch();
-  return cudaLaunchCooperativeKernel((void*)band_lu_kernel, dim3(q * P), dim3(256), args, smem, s);
+  return cudaLaunchCooperativeKernel((void*)band_lu_kernel, dim3(q * P), dim3(512), args, smem, s);
 }
 
 // ----------------------------------------------------------------------------------------------
