@@ -112,7 +112,7 @@ typedef struct {
  * shifts/weights (Thm 2, p roots of z^p = -1), assembles K_i = p_i B - A for all
  * q poles into LAPACK band storage (kl = ku = max|offset|, ldab = 3*kl + 1) and
  * factors all of them with partial pivoting in one cooperative launch
- * (Alg. 1 lines 1-4). Requires p >= 1, q >= 1, radius > 0, 1 <= opts->k <= n.
+ * (set-up steps of Alg. 1). Requires p >= 1, q >= 1, radius > 0, 1 <= opts->k <= n.
  * Returns IE_ERR_SINGULAR if a pivot is exactly zero (the handle is still
  * created and must be destroyed). Synchronises the stream before returning. */
 ie_status ie_create(const ie_pencil* pencil, ie_complex center, double radius,
@@ -134,12 +134,12 @@ ie_status ie_filter_apply(ie_handle h, const ie_complex* Y_any, int64_t ldy, int
                           ie_complex* U_any, int64_t ldu, void* stream);
 
 /* ie_apply_G: the inner operator alone, GV = G(V) = sum_i w_i K_i^{-1} B V
- * (Eq. linearsolve2; Alg. 1 line 5). V_any, GV_any: n x k (k <= opts.k). */
+ * (Eq. linearsolve2; Alg. 1). V_any, GV_any: n x k (k <= opts.k). */
 ie_status ie_apply_G(ie_handle h, const ie_complex* V_any, int64_t ldv, int32_t k,
                      ie_complex* GV_any, int64_t ldgv, void* stream);
 
 /* ie_hsrr: the harmonic Rayleigh-Ritz step HSRR(A, B, U, sigma) (Sec. 2.1,
- * Alg. SIsketch lines 4-7): V = orth(U) (CGS2 with rank guard), W = orth(AV - sigma BV),
+ * extraction steps of Alg. SIsketch): V = orth(U) (CGS2 with rank guard), W = orth(AV - sigma BV),
  * QZ of (W^*AV, W^*BV), lambda_i = (H_A)_ii/(H_B)_ii, x_i = V P_R V_R(:,i) scaled
  * to unit norm; e_i (Eq. rel-error) and rho_i = ||Ax - lambda Bx|| /
  * ((||A||_1 + |lambda| ||B||_1) ||x||). Outputs in QZ order (no sorting):

@@ -52,7 +52,7 @@ def solve(A, B, c: complex, r: float, p: int, q: int, Y0: np.ndarray, driver: in
     sigma = c if sigma is None else sigma           # sigma = c (Sec. 6 preamble)
     t0 = time.perf_counter()
     if G is None:
-        G = InnerOperator(A, B, c, r, q)            # Alg. 1/2 lines 1-5
+        G = InnerOperator(A, B, c, r, q)            # set-up of Alg. 1/2
     t_factor = time.perf_counter() - t0
     nA, nB = norm1(A), norm1(B)
     rng = np.random.Generator(np.random.PCG64(seed + 7))
@@ -64,9 +64,9 @@ def solve(A, B, c: complex, r: float, p: int, q: int, Y0: np.ndarray, driver: in
     if driver == 1:
         res = None
         for t in range(1, max_outer + 1):
-            U, st = filter_apply(G, Y, p, gmres_tol, m_max, return_stats=True)   # lines 8-10
-            res = hsrr(A, B, U, sigma, c, r, nA, nB, rng)                        # line 11
-            filt, order = _finish(res, c, tau_g, r)                              # line 12
+            U, st = filter_apply(G, Y, p, gmres_tol, m_max, return_stats=True)   # filter step
+            res = hsrr(A, B, U, sigma, c, r, nA, nB, rng)                        # extraction step
+            filt, order = _finish(res, c, tau_g, r)                              # ghost filter
             n_found = int(filt.sum())
             hist.append({"t": t, "n_found": n_found, "gmres_iters": st["gmres_iters"],
                          "max_rho_filtered": float(np.max(res["rho"][filt])) if n_found else 0.0,
@@ -77,18 +77,18 @@ def solve(A, B, c: complex, r: float, p: int, q: int, Y0: np.ndarray, driver: in
             prev = n_found
             Y = res["X"]                               # Y <- Ritz vectors
     elif driver == 2:
-        Yt = G.apply(Y)                                # Alg. 2 line 7
+        Yt = G.apply(Y)                                # Alg. 2: G(Y) once
         cols = [ColumnKrylov(G.apply, Yt[:, j], m_max) for j in range(k)]
         pc = p
         res = None
         for t in range(1, max_outer + 1):
             s, cw, odd = outer_shifts_weights(pc)
             iters = []
-            for kr in cols:                             # line 9: all shifts, reuse + expand
+            for kr in cols:                             # all shifts, reuse + expand
                 kr.run(s, gmres_tol)
                 iters.append(kr.J)
-            U = np.stack([kr.combine(s, cw, odd) for kr in cols], axis=1)   # line 10
-            res = hsrr(A, B, U, sigma, c, r, nA, nB, rng)                  # line 11
+            U = np.stack([kr.combine(s, cw, odd) for kr in cols], axis=1)   # combination step
+            res = hsrr(A, B, U, sigma, c, r, nA, nB, rng)                  # extraction step
             filt, order = _finish(res, c, tau_g, r)
             n_found = int(filt.sum())
             hist.append({"t": t, "n_found": n_found, "gmres_iters": iters,
@@ -98,7 +98,7 @@ def solve(A, B, c: complex, r: float, p: int, q: int, Y0: np.ndarray, driver: in
                 status = "ok"
                 break
             prev = n_found
-            pc *= 2                                     # line 13
+            pc *= 2                                     # doubling step
     else:
         raise ValueError("driver must be 1 or 2")
     filt, order = _finish(res, c, tau_g, r)

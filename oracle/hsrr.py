@@ -1,5 +1,5 @@
-"""Harmonic subspace Rayleigh-Ritz extraction "HSRR" (Sec. 2.1, Alg. SIsketch
-lines 4-7) and the error measures of Sec. 3.2.
+"""Harmonic subspace Rayleigh-Ritz extraction "HSRR" (Sec. 2.1, the extraction
+steps of Alg. SIsketch) and the error measures of Sec. 3.2.
 
     V = orth(U);  W = orth(A V - sigma B V);
     (W^* A V, W^* B V) -> QZ: P_L^* (W^*AV) P_R = H_A, P_L^* (W^*BV) P_R = H_B;
@@ -95,7 +95,7 @@ def residuals(A, B, lam: np.ndarray, X: np.ndarray, c: complex, r: float,
 
 def hsrr(A, B, U: np.ndarray, sigma: complex, c: complex, r: float,
          normA: float, normB: float, rng: np.random.Generator | None = None) -> dict:
-    """[Y, Lambda, X] = HSRR(A, B, U, sigma) (Alg. SIsketch lines 4-7) plus errors."""
+    """[Y, Lambda, X] = HSRR(A, B, U, sigma) (extraction steps of Alg. SIsketch) plus errors."""
     V, rep_v = orth_cgs2(U, rng)
     AV = A @ V
     BV = B @ V

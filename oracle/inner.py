@@ -1,4 +1,4 @@
-"""Inner operator G (Sec. 3.2, Eq. linearsolve2; Alg. 1 lines 2-5).
+"""Inner operator G (Sec. 3.2, Eq. linearsolve2; the set-up steps of Alg. 1).
 
 K_i = p_i B - A for the q inner trapezoidal poles, each factorised once
 (sparse LU, SciPy SuperLU, as the paper uses MATLAB's default sparse LU,
@@ -22,7 +22,7 @@ class InnerOperator:
         self.poles, self.weights = trapezoid_poles_weights(c, r, q)
         self.factors = []
         for p in self.poles:
-            K = (p * B - A).tocsc()           # K_i = p_i B - A (Alg. 1 line 3)
+            K = (p * B - A).tocsc()           # K_i = p_i B - A (Alg. 1)
             self.factors.append(spla.splu(K))
         self.n_applies = 0                    # columns G has been applied to
 

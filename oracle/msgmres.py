@@ -1,5 +1,5 @@
 """Outer rational function by multi-shift GMRES (Sec. 3.2, Eq. linearsolve1abs;
-Alg. 1 lines 7-9; Alg. 2 lines 8-9).
+the filter steps of Alg. 1 and Alg. 2).
 
 For one column ytilde = G(y) the Krylov space K_J(G, ytilde) is built once by
 Arnoldi and shared by every outer shift, because K_J(G - sI, y) = K_J(G, y) and
@@ -108,7 +108,7 @@ class ColumnKrylov:
 
 def filter_apply(G, Y: np.ndarray, p: int, tol: float = 1e-12, m_max: int = 100,
                  return_stats: bool = False):
-    """U = R_{c,r,pq}(B^{-1}A) Y by the composite rule (Alg. 1 lines 7-9):
+    """U = R_{c,r,pq}(B^{-1}A) Y by the composite rule (filter step of Alg. 1):
     Ytilde = G(Y); per column multi-shift GMRES for the p outer shifts; combine."""
     s, c, odd = outer_shifts_weights(p)
     Y = np.asarray(Y, dtype=np.complex128)

@@ -1,6 +1,6 @@
 // C ABI of the interior eigensolver (include/ie.h): handle life cycle, the composite-rule
-// coefficients (Eq. pwtp; Thm 2), the filter (Alg. 1 lines 7-9), HSRR (Alg. SIsketch lines
-// 4-7) and the two drivers (Alg. 1, Alg. 2). Host code orchestrates kernels on one stream;
+// coefficients (Eq. pwtp; Thm 2), the filter (Alg. 1), HSRR (extraction steps of Alg.
+// SIsketch) and the two drivers (Alg. 1, Alg. 2). Host code orchestrates kernels on one stream;
 // the GMRES loop reads k residuals back per Arnoldi step for its convergence test.
 #include <algorithm>
 #include <cmath>
@@ -572,7 +572,7 @@ static ie_status apply_G_mixed(ie_handle h, int k, cplx* GV, int64_t ldg, cudaSt
 
 // ------------------------------ filter (multi-shift GMRES) -----------------------------------
 // U = sum_j c_j (s_j I - G)^{-1} Ytilde (+ odd Ytilde). With reuse, the Krylov spaces of the
-// previous call are kept and only extended (Alg. 2 line 9).
+// previous call are kept and only extended (Alg. 2).
 static ie_status filter_dev(ie_handle h, const cplx* Y, int64_t ldy, int k, cplx* U, int64_t ldu,
                             int p_use, bool reuse, cudaStream_t s, bool* noconv) {
   const int64_t n = h->n;
@@ -836,9 +836,9 @@ extern "C" ie_status ie_solve(ie_handle h, const ie_complex* Y0_any, int64_t ldy
     cudaEventRecord(e0, s);
     bool nc = false;
     if (h->opts.driver == 1) {
-      st = filter_dev(h, h->Yb, n, k, h->Ub, n, h->p, false, s, &nc);       // Alg. 1 lines 8-10
+      st = filter_dev(h, h->Yb, n, k, h->Ub, n, h->p, false, s, &nc);       // Alg. 1 filter step
     } else {
-      st = filter_dev(h, h->Yb, n, k, h->Ub, n, pc, t > 1, s, &nc);         // Alg. 2 lines 9-10
+      st = filter_dev(h, h->Yb, n, k, h->Ub, n, pc, t > 1, s, &nc);         // Alg. 2 filter step
     }
     cudaEventRecord(e1, s);
     if (st != IE_OK) break;
@@ -848,13 +848,13 @@ extern "C" ie_status ie_solve(ie_handle h, const ie_complex* Y0_any, int64_t ldy
     S.t_filter_ms += ms;
     any_noconv |= nc;
     cudaEventRecord(e0, s);
-    st = hsrr_dev(h, h->Ub, n, k, s, lam, e, rho);                           // line 11
+    st = hsrr_dev(h, h->Ub, n, k, s, lam, e, rho);                           // extraction step
     cudaEventRecord(e1, s);
     if (st != IE_OK) break;
     cudaStreamSynchronize(s);
     cudaEventElapsedTime(&ms, e0, e1);
     S.t_hsrr_ms += ms;
-    // ghost filter and stop test (line 12; Sec. 3.2)
+    // ghost filter and stop test (Sec. 3.2)
     filt.assign(k, 0);
     nf = 0;
     bool all_conv = true;
@@ -878,7 +878,7 @@ extern "C" ie_status ie_solve(ie_handle h, const ie_complex* Y0_any, int64_t ldy
     if (h->opts.driver == 1) {
       launch_copy_cols(n, k, h->Xh, n, h->Yb, n, s);                         // Y <- Ritz vectors
     } else {
-      pc *= 2;                                                               // line 13
+      pc *= 2;                                                               // doubling step
     }
   }
   cudaEventDestroy(e0);

@@ -1,4 +1,4 @@
-// Harmonic Rayleigh-Ritz extraction "HSRR" (Sec. 2.1, Alg. SIsketch lines 4-7):
+// Harmonic Rayleigh-Ritz extraction "HSRR" (Sec. 2.1, extraction steps of Alg. SIsketch):
 //   V = orth(U), W = orth(A V - sigma B V)   -- CGS2 with a rank guard
 //   (W^* A V, W^* B V)                       -- Gram contractions over n
 //   QZ: P_L^* (.) P_R = (H_A, H_B); lambda_i = (H_A)_ii / (H_B)_ii; x_i = V P_R V_R(:, i)

@@ -1,5 +1,5 @@
-// Outer rational function by multi-shift GMRES (Sec. 3.2, Eq. linearsolve1abs; Alg. 1 lines
-// 7-9): one Arnoldi basis of G per column, orthogonalised by CGS2 (classical Gram-Schmidt,
+// Outer rational function by multi-shift GMRES (Sec. 3.2, Eq. linearsolve1abs; filter step
+// of Alg. 1): one Arnoldi basis of G per column, orthogonalised by CGS2 (classical Gram-Schmidt,
 // twice), shared by all outer shifts s_j, since (G - sI) V_J = V_{J+1} (Hbar_J - s Ibar_J).
 // Per (column, shift) the QR factorisation of Hbar - s Ibar is updated by Givens rotations;
 // the last rotated right-hand-side entry is the GMRES residual.
