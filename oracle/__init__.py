@@ -18,6 +18,9 @@ Pins (tests/test_oracle_*.py), each against something other than the oracle:
              pq-pole simple rule and X R_pq(Lambda) X^{-1} Y (Thm 2).
   hsrr / drivers - tiny pencils with planted spectra; dense QZ on the small
              convection-diffusion pencil; eigen-residuals.
+  adjoint  - dense spectral definition for the adjoint pencil; the identity
+             B^H G_adj = G^H B^H; LAPACK left eigenvectors; central finite
+             differences of dense eigenvalues for the sensitivities and the VJP.
 No function is "parity unpinned".
 """
-from . import coeffs, pencil, inner, msgmres, hsrr, drivers  # noqa: F401
+from . import coeffs, pencil, inner, msgmres, hsrr, drivers, adjoint  # noqa: F401

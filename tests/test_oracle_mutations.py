@@ -73,3 +73,80 @@ def test_wrong_shift_sign_is_caught(monkeypatch):
     good = msgmres.ColumnKrylov.solve_shift
     monkeypatch.setattr(msgmres.ColumnKrylov, "solve_shift", lambda self, s: good(self, -s))
     assert _gmres_error() > 1e-4
+
+
+# ---------------------------------------------------------------- adjoint / sensitivities
+def _small_pencil():
+    pen = ie_inputs.make_pencil(6, seed=4)
+    return pencil.pencil_matrices(pen)
+
+
+def _adjoint_identity_error():
+    """B^H G_adj V against G^H B^H V (the identity pin of the adjoint operator)."""
+    from oracle import adjoint
+    A, B = _small_pencil()
+    n = A.shape[0]
+    c, r = A.diagonal().mean(), 20.0
+    Gd = inner.InnerOperator(A, B, c, r, 4).apply(np.eye(n, dtype=np.complex128))
+    V = ie_inputs.random_block(n, 2, seed=3)
+    Bh = B.toarray().conj().T
+    lhs = Bh @ adjoint.adjoint_inner(A, B, c, r, 4).apply(V)
+    rhs = Gd.conj().T @ (Bh @ V)
+    return np.linalg.norm(lhs - rhs) / np.linalg.norm(rhs)
+
+
+def _sensitivity_error():
+    """Largest relative gap between diag_sensitivity and central differences of dense
+    eigenvalues on a 36 x 36 pencil (the finite-difference pin)."""
+    import scipy.linalg as sla
+    from oracle import adjoint
+    A, B = _small_pencil()
+    Ad, Bd = A.toarray(), B.toarray()
+    lam, VL, VR = sla.eig(Ad, Bd, left=True, right=True)
+    gaps = np.array([np.min(np.abs(np.delete(lam, i) - lam[i])) for i in range(len(lam))])
+    sel = np.argsort(-gaps)[:3]
+    S = adjoint.diag_sensitivity(B, VR[:, sel], VL[:, sel], alpha=1j)
+    worst = 0.0
+    for j in (0, 7, 20):
+        d = []
+        for t in (1e-3, -1e-3):
+            Ap = Ad.copy()
+            Ap[j, j] += 1j * t
+            lt = np.linalg.eigvals(np.linalg.solve(Bd, Ap))
+            d.append(np.array([lt[np.argmin(np.abs(lt - lam[i]))] for i in sel]))
+        fd = (d[0] - d[1]) / 2e-3
+        worst = max(worst, float(np.max(np.abs(S[j] - fd) / np.abs(fd))))
+    return worst
+
+
+def test_adjoint_pins_pass_unmutated():
+    assert _adjoint_identity_error() < 1e-11
+    assert _sensitivity_error() < 1e-5
+
+
+def test_unconjugated_adjoint_nodes_are_caught(monkeypatch):
+    from oracle import adjoint
+
+    def bad(A, B, c, r, q):                  # the primal disk's nodes for the adjoint pencil
+        AH, BH = adjoint.adjoint_pencil(A, B)
+        return inner.InnerOperator(AH, BH, c, r, q)
+    monkeypatch.setattr(adjoint, "adjoint_inner", bad)
+    assert _adjoint_identity_error() > 1e-3
+
+
+def test_unconjugated_left_vector_is_caught(monkeypatch):
+    from oracle import adjoint
+    good = adjoint.diag_sensitivity
+    monkeypatch.setattr(adjoint, "diag_sensitivity",
+                        lambda B, X, Y, alpha=1.0: good(B, X, np.conj(Y), alpha))
+    assert _sensitivity_error() > 1e-3
+
+
+def test_denominator_without_b_is_caught(monkeypatch):
+    from oracle import adjoint
+
+    def bad(B, X, Y, alpha=1.0):             # y^H x instead of y^H B x
+        den = np.sum(np.conj(Y) * X, axis=0)
+        return alpha * np.conj(Y) * X / den[None, :]
+    monkeypatch.setattr(adjoint, "diag_sensitivity", bad)
+    assert _sensitivity_error() > 1e-3
