@@ -49,6 +49,9 @@ def parse():
     ap.add_argument("--mixed", type=int, default=1,
                     help="1 (with --precision 0): also report the mixed-precision path on the same "
                          "workload (throughput and time to all eigenpairs at the same residual)")
+    ap.add_argument("--sens", type=int, default=1,
+                    help="1: also time left eigenvectors + eigenvalue sensitivities (adjoint "
+                         "pencil) and the conjugate-transpose band-solve kernel")
     ap.add_argument("--precision", type=int, default=0, choices=[0, 1],
                     help="0: complex128 factors and solves; 1: complex64 factors, FP32 solves, "
                          "FP64 refinement")
@@ -302,6 +305,10 @@ def run_native(args):
                                     "peak_tflops": FP32_PEAK_TFLOPS},
                  "time_to_all_eigenpairs": time_solves(1) if args.solve else None}
 
+    sens = None
+    if args.sens and rank == 0:
+        sens = time_sensitivities(ie, w, pen, A_d, B_d, device, stream, Xd)
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         cpu = cpu_baseline(args.workload)
@@ -344,6 +351,7 @@ def run_native(args):
             "gpu_launches": gpu_launches,
             "time_to_all_eigenpairs": solves,
             "mixed_precision": mixed,
+            "sensitivities": sens,
             "e2e": e2e,
             "clocks": clk.summary(),
             "cpu_baseline": cpu,
@@ -351,6 +359,82 @@ def run_native(args):
         print(json.dumps(line))
     if dist is not None:
         dist.destroy_process_group()
+
+
+def time_sensitivities(ie, w, pen, A_d, B_d, device, stream, Xd):
+    """Eigenvalue derivatives on the same workload: right eigenpairs (ie_solve), left
+    eigenvectors by the adjoint pencil (ie_solve_left) and the gradient of the seeded loss
+    J = sum_i w_i Re(lambda_i), w_i ~ U(0, 1), with respect to gamma at every grid node
+    (ie_eig_sensitivity), with the mixed-precision handle; then the complex128 conjugate-
+    transpose band-solve kernel alone (ie_apply_GH on k columns) for its roofline."""
+    import torch
+
+    import ie_inputs
+    n, k, p, q = pen.n, w["k"], w["p"], w["q"]
+    out = {"loss": "J = sum_i w_i Re(lambda_i) over the eigenvalues in D, w_i ~ U(0,1) (seed 5); "
+                   "dJ/dgamma at all n nodes"}
+    om = ie.ie_opts_default(k=k, m_max=150, precision=1, adjoint=1)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    st, h = ie.ie_create(n, pen.offsets, A_d, B_d, w["center"], w["radius"], p, q, om, stream)
+    if st != ie.IE_OK:
+        return {"error": ie.ie_status_str(st)}
+    torch.cuda.synchronize()
+    out["create_s"] = time.perf_counter() - t0
+    Y0 = ie_inputs.orthonormal_random_block(n, k, seed=w["seed"])
+    Y0d = torch.from_numpy(np.ascontiguousarray(Y0.T)).to(device).T
+    t0 = time.perf_counter()
+    st1, lam, rho, e, nf, _ = ie.ie_solve(h, Y0d, Xd, k, stream)
+    torch.cuda.synchronize()
+    out["right_solve_s"] = time.perf_counter() - t0
+    Yl = torch.zeros((k, n), dtype=torch.complex128, device=device).T
+    t0 = time.perf_counter()
+    st2, ll, rl, sst = ie.ie_solve_left(h, lam[:nf], Yl, None, stream)
+    torch.cuda.synchronize()
+    out["left_solve_s"] = time.perf_counter() - t0
+    gbar = np.random.default_rng(5).uniform(0, 1, nf) + 0j
+    grad = torch.zeros(n, dtype=torch.float64, device=device)
+    ie.ie_eig_sensitivity(h, Xd[:, :nf], Yl[:, :nf], 1j, None, gbar, grad, stream)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    st3 = ie.ie_eig_sensitivity(h, Xd[:, :nf], Yl[:, :nf], 1j, None, gbar, grad, stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    out.update({"status": [ie.ie_status_str(x) for x in (st1, st2, st3)], "n_pairs": nf,
+                "max_rho_right": float(np.max(rho[:nf])) if nf else None,
+                "max_rho_left": float(np.max(rl)) if nf else None,
+                "adjoint_outer_iters": sst["outer_iters"],
+                "gradient_ms": e0.elapsed_time(e1),
+                "grad_norm": float(torch.linalg.vector_norm(grad).item())})
+    ie.ie_destroy(h)
+    # the complex128 conjugate-transpose solve kernel, timed by the library per launch
+    o64 = ie.ie_opts_default(k=k, m_max=150, precision=0, adjoint=1)
+    st, h = ie.ie_create(n, pen.offsets, A_d, B_d, w["center"], w["radius"], p, q, o64, stream)
+    if st != ie.IE_OK:
+        out["band_solve_adj_c128"] = {"error": ie.ie_status_str(st)}
+        return out
+    V = torch.from_numpy(np.ascontiguousarray(ie_inputs.random_block(n, k, seed=3).T)).to(device).T
+    GV = torch.zeros((k, n), dtype=torch.complex128, device=device).T
+    for _ in range(2):   # warm-up
+        ie.ie_apply_GH(h, V, GV, stream)
+    torch.cuda.synchronize()
+    _, a0 = ie.ie_get_stats(h)
+    for _ in range(3):
+        ie.ie_apply_GH(h, V, GV, stream)
+    torch.cuda.synchronize()
+    _, a1 = ie.ie_get_stats(h)
+    la = a1["adj_launches"] - a0["adj_launches"]
+    ms = a1["t_adj_ms"] - a0["t_adj_ms"]
+    fl = a1["adj_flops"] - a0["adj_flops"]
+    ach = fl / (ms / 1e3) / 1e12 if ms > 0 else None
+    out["band_solve_adj_c128"] = {"kernel": "band_solve_adj_kernel", "k": k, "launches": la,
+                                  "avg_launch_ms": ms / la if la else None,
+                                  "achieved_tflops": ach, "peak_tflops": FP64_PEAK_TFLOPS,
+                                  "frac": ach / FP64_PEAK_TFLOPS if ach else None}
+    ie.ie_destroy(h)
+    return out
 
 
 # ------------------------------------------------------------------ CPU oracle

@@ -79,10 +79,15 @@ typedef struct {
                              factorisation), the triangular solves run in FP32, and each
                              K_i^{-1} b is refined in FP64: x += K~_i^{-1} (b - K_i x) */
   int32_t refine_steps;   /* FP64 refinement steps per solve when precision = 1 (default 2) */
+  int32_t adjoint;        /* 1: also prepare the conjugate-transpose solves K_i^{-H} with the same
+                             factors (ie_apply_GH, ie_solve_left): the adjoint pencil in DIA
+                             form, a row-major copy of each U factor (q * n * 2*kl entries,
+                             complex128 or complex64 as the factors) and a 16 x 24 transform
+                             per 8-row panel and pole. Default 0. Not in the paper. */
 } ie_opts;
 
 /* Fills defaults: k=16, driver=1, m_max=100, max_outer=10, tau_g=1e-2, tau=1e-10,
- * gmres_tol=1e-12, sigma = center, seed = 0, precision = 0, refine_steps = 2. */
+ * gmres_tol=1e-12, sigma = center, seed = 0, precision = 0, refine_steps = 2, adjoint = 0. */
 void ie_opts_default(ie_opts* opts);
 
 /* Counters and timings of the last ie_solve / ie_filter_apply on a handle. */
@@ -106,6 +111,9 @@ typedef struct {
   int64_t solve32_launches;/* complex64 band-solve launches (precision = 1) since create */
   double t_solve32_ms;     /* their summed device time */
   double solve32_flops;    /* their algorithmic flops (same count as solve_flops, in FP32) */
+  int64_t adj_launches;    /* conjugate-transpose band-solve launches since create (either precision) */
+  double t_adj_ms;         /* their summed device time */
+  double adj_flops;        /* their algorithmic flops (same count per launch as the forward solve) */
 } ie_stats;
 
 /* ie_create: computes the inner poles/weights (Eq. pwtp, q points) and the outer
@@ -207,6 +215,54 @@ ie_status ie_get_stats(ie_handle h, ie_stats* out);
 #define IE_STATIC_SCRATCH_BYTES (32u * 1024u * 1024u)
 ie_status ie_apply_G_static(ie_handle h, const ie_complex* d_V, int64_t ldv, int32_t k,
                             ie_complex* d_GV, int64_t ldgv, void* stream);
+
+/* ---------------------------------------------------------------------------------------
+ * Adjoint pencil, left eigenvectors and eigenvalue sensitivities. The paper computes right
+ * eigenpairs only; these entry points carry its method over to the adjoint pencil.
+ * A left eigenvector y of (A, B) for lambda (y^H A = lambda y^H B) is a right eigenvector of
+ * (A^H, B^H) for conj(lambda). The trapezoidal nodes and weights of the conjugate disk are
+ * the conjugates of p_i, w_i (Eq. pwtp; the angles (2i-1) pi / q are closed under negation),
+ * and conj(p_i) B^H - A^H = K_i^H, so the adjoint pencil's inner operator reuses the band
+ * factors of K_i = P_i^T L_i U_i through K_i^{-H} = P_i^T L_i^{-H} U_i^{-H}.
+ * ie_apply_GH and ie_solve_left need a handle created with opts.adjoint = 1 (else
+ * IE_ERR_ARG); ie_eig_sensitivity works on any handle. */
+
+/* ie_apply_GH: GV = G_adj(V) = sum_i conj(w_i) K_i^{-H} B^H V, the inner operator
+ * (Eq. linearsolve2) of (A^H, B^H) on the disk |z - conj(center)| < radius.
+ * V_any, GV_any: n x k (k <= opts.k), column-major. Mixed-precision handles refine each
+ * K_i^{-H} b in FP64 like ie_apply_G. */
+ie_status ie_apply_GH(ie_handle h, const ie_complex* V_any, int64_t ldv, int32_t k,
+                      ie_complex* GV_any, int64_t ldgv, void* stream);
+
+/* ie_solve_left: left eigenvectors for the nl eigenvalues h_lambda[0..nl) of (A, B)
+ * (typically the first n_found outputs of ie_solve; 1 <= nl <= opts.k). Runs the handle's
+ * driver (opts.driver, same options) on (A^H, B^H) over the conjugate disk, then pairs each
+ * requested eigenvalue with the nearest conjugated adjoint eigenvalue (one-to-one).
+ * Outputs: Y_any column i (unit 2-norm) is the left vector of h_lambda[i];
+ * h_lambda_left[i] (host, nullable) the paired adjoint eigenvalue conjugated back;
+ * h_rho_left[i] (host, nullable) its residual rho for (A^H, B^H) (Sec. 3.2 definition).
+ * Y0_any: n x opts.k starting block or NULL (seeded random). stats: nullable.
+ * Returns IE_ERR_NOCONV if the adjoint driver missed its stop test, or if a requested
+ * eigenvalue has no partner within 1e-8 * max(|lambda|, radius) or two requests share one
+ * (all outputs are still written). */
+ie_status ie_solve_left(ie_handle h, const ie_complex* h_lambda, int32_t nl,
+                        const ie_complex* Y0_any, int64_t ldy0, ie_complex* Y_any, int64_t ldy,
+                        ie_complex* h_lambda_left, double* h_rho_left, ie_stats* stats,
+                        void* stream);
+
+/* ie_eig_sensitivity: first-order sensitivities of nf simple eigenvalues to the diagonal of
+ * A, from right vectors X and left vectors Y (column i of each belongs to eigenvalue i):
+ *   S[j, i] = d lambda_i / d t_j = alpha * conj(Y[j, i]) * X[j, i] / (Y[:, i]^H B X[:, i])
+ * for A_jj(t) = A_jj + alpha t_j (alpha = i for a parameter entering as + i gamma_j), and
+ * the vector-Jacobian product of a real loss J(lambda) with h_gbar[i] = dJ/dRe lambda_i +
+ * i dJ/dIm lambda_i:  grad[j] = Re sum_i conj(gbar_i) S[j, i].
+ * X_any, Y_any: n x nf (1 <= nf <= opts.k). S_any: n x nf (lds >= n) or NULL.
+ * h_gbar: host, nf entries, or NULL (then grad_any must be NULL). grad_any: n doubles or NULL.
+ * S and grad do not depend on the scaling of X or Y. */
+ie_status ie_eig_sensitivity(ie_handle h, const ie_complex* X_any, int64_t ldx,
+                             const ie_complex* Y_any, int64_t ldy, int32_t nf, ie_complex alpha,
+                             ie_complex* S_any, int64_t lds, const ie_complex* h_gbar,
+                             double* grad_any, void* stream);
 
 #ifdef __cplusplus
 }

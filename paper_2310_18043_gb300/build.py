@@ -15,7 +15,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libie.so")
-SOURCES = ["ie_band.cu", "ie_solve.cu", "ie_krylov.cu", "ie_hsrr.cu", "ie_capi.cu", "ie_static.cu"]
+SOURCES = ["ie_band.cu", "ie_solve.cu", "ie_adjoint.cu", "ie_krylov.cu", "ie_hsrr.cu", "ie_capi.cu",
+           "ie_static.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]
 
@@ -37,7 +38,7 @@ def _stale(obj: str, deps: list[str]) -> bool:
 def build(verbose: bool = False, ptxas_v: bool = False) -> str:
     os.makedirs(BUILD, exist_ok=True)
     nvcc = _nvcc()
-    headers = [os.path.join(CSRC, "ie_internal.cuh"),
+    headers = [os.path.join(CSRC, "ie_internal.cuh"), os.path.join(CSRC, "ie_bulk.cuh"),
                os.path.join(HERE, "..", "include", "ie.h")]
     objs, jobs = [], []
     for src in SOURCES:

@@ -74,6 +74,26 @@ struct ie_handle_s {
   cplx* Uinvb = nullptr;   // q * npanel * 64: inverses of U's 8x8 diagonal blocks
   float2* T32 = nullptr;   // complex64 copies (precision = 1)
   float2* Ub32 = nullptr;
+  // adjoint pencil (opts.adjoint = 1): (A^H, B^H), conjugated coefficients, U by rows and
+  // the per-panel transforms of the conjugate-transpose L sweep
+  bool adj = false;
+  int side = 0;            // 0: (A, B) on D(c, r); 1: (A^H, B^H) on D(conj c, r)
+  DiaDev PH{};
+  cplx* d_AH = nullptr;
+  cplx* d_BH = nullptr;
+  cplx* d_pconj = nullptr;
+  cplx* d_wconj = nullptr;
+  double normAH = 0, normBH = 0;
+  cplx* Ut64 = nullptr;    // q * n_pad * kv
+  cplx* Madj64 = nullptr;  // q * npanel * 384
+  float2* Ut32 = nullptr;
+  float2* Madj32 = nullptr;
+  double* d_grad = nullptr;   // n, ie_eig_sensitivity staging (allocated on first use)
+  const DiaDev& pen() const { return side ? PH : P; }
+  zc ctr() const { return side ? std::conj(center) : center; }
+  zc sig() const { return side ? std::conj(sigma) : sigma; }
+  double nA() const { return side ? normAH : normA; }
+  double nB() const { return side ? normBH : normB; }
   unsigned* bar = nullptr;
   int* status = nullptr;
   int lu_ctas = 0;
@@ -130,11 +150,12 @@ struct ie_handle_s {
   ie_stats stats{};
   int64_t g_columns = 0;
   // band-solve launch timing: event pairs pending until the next stream synchronisation
-  struct SolveRec { cudaEvent_t a, b; double flops, bytes; int fp32; };
+  struct SolveRec { cudaEvent_t a, b; double flops, bytes; int fp32, adj; };
   std::vector<SolveRec> pending;
   std::vector<cudaEvent_t> event_pool;
-  int64_t solve_launches = 0, solve32_launches = 0;
+  int64_t solve_launches = 0, solve32_launches = 0, adj_launches = 0;
   double t_solve_ms = 0, solve_flops = 0, solve_bytes = 0, t_solve32_ms = 0, solve32_flops = 0;
+  double t_adj_ms = 0, adj_flops = 0;
   cudaEvent_t get_event() {
     if (!event_pool.empty()) { cudaEvent_t e = event_pool.back(); event_pool.pop_back(); return e; }
     cudaEvent_t e;
@@ -182,6 +203,7 @@ extern "C" void ie_opts_default(ie_opts* o) {
   o->seed = 0;
   o->precision = 0;
   o->refine_steps = 2;
+  o->adjoint = 0;
 }
 
 extern "C" const char* ie_status_str(ie_status s) {
@@ -296,6 +318,49 @@ static ie_status alloc_workspace(ie_handle h) {
   return IE_OK;
 }
 
+// Adjoint pencil for ie_apply_GH / ie_solve_left, from the complex128 band factors (AB must
+// still be present): (A^H, B^H) and their norms, conj(p_i), conj(w_i), U by rows and the
+// phase-2 transforms, in the handle's factor precision.
+static ie_status setup_adjoint(ie_handle h, cudaStream_t s) {
+  const int q = h->q;
+  const size_t nd = (size_t)h->ndiag * h->n, np = (size_t)(h->n_pad / 8);
+  CK(h->alloc(&h->d_AH, nd));
+  CK(h->alloc(&h->d_BH, nd));
+  launch_dia_adjoint(h->P, h->d_AH, h->d_BH, &h->PH, s);
+  double* dn = nullptr;
+  CK(h->alloc(&dn, 2));
+  launch_norm1_cols(h->PH, 0, dn, nullptr, s);
+  launch_norm1_cols(h->PH, 1, dn + 1, nullptr, s);
+  double hn[2];
+  CK(cudaMemcpyAsync(hn, dn, sizeof(hn), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  h->normAH = hn[0];
+  h->normBH = hn[1];
+  std::vector<cplx> pc(q), wc(q);
+  for (int i = 0; i < q; ++i) {
+    pc[i] = to_c(std::conj(h->poles[i]));
+    wc[i] = to_c(std::conj(h->weights[i]));
+  }
+  CK(h->alloc(&h->d_pconj, q));
+  CK(h->alloc(&h->d_wconj, q));
+  CK(cudaMemcpyAsync(h->d_pconj, pc.data(), sizeof(cplx) * q, cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(h->d_wconj, wc.data(), sizeof(cplx) * q, cudaMemcpyHostToDevice, s));
+  const size_t nu = (size_t)q * h->n_pad * h->kv, nm = (size_t)q * np * 384;
+  if (h->precision == 0) {
+    CK(h->alloc(&h->Ut64, nu));
+    CK(h->alloc(&h->Madj64, nm));
+  } else {
+    CK(h->alloc(&h->Ut32, nu));
+    CK(h->alloc(&h->Madj32, nm));
+  }
+  launch_u_rows(q, h->n, h->n_pad, h->kl, h->ldab, h->AB, h->Ut64, h->Ut32, s);
+  launch_adj_transforms(q, h->n, h->n_pad, h->kl, h->ldab, h->AB, h->piv, h->Hb, h->Madj64,
+                        h->Madj32, s);
+  CK(cudaStreamSynchronize(s));
+  h->adj = true;
+  return IE_OK;
+}
+
 // ------------------------------ create / destroy -------------------------------------------------
 extern "C" ie_status ie_create(const ie_pencil* pen, ie_complex center, double radius, int32_t p,
                                int32_t q, const ie_opts* opts_in, void* stream, ie_handle* out) {
@@ -310,7 +375,7 @@ extern "C" ie_status ie_create(const ie_pencil* pen, ie_complex center, double r
     return IE_ERR_ARG;
   if (!(opts.gmres_tol > 0) || !(opts.tau > 0) || !(opts.tau_g > 0)) return IE_ERR_ARG;
   if ((opts.precision != 0 && opts.precision != 1) || opts.refine_steps < 0 ||
-      opts.refine_steps > 20)
+      opts.refine_steps > 20 || (opts.adjoint != 0 && opts.adjoint != 1))
     return IE_ERR_ARG;
   int kl = 0;
   for (int d = 0; d < pen->ndiag; ++d) {
@@ -423,6 +488,10 @@ extern "C" ie_status ie_create(const ie_pencil* pen, ie_complex center, double r
     launch_block_transforms(q, h->n, h->n_pad, kl, h->ldab, h->AB, h->piv, h->dinv, h->Tb, h->Hb,
                             h->Uinvb, h->T32, h->Ub32, s);
     if (cudaStreamSynchronize(s) != cudaSuccess) return fail(IE_ERR_CUDA);
+    if (opts.adjoint) {
+      ie_status as = setup_adjoint(h, s);
+      if (as != IE_OK) return fail(as);
+    }
   }
   ie_status ws = alloc_workspace(h);
   if (ws != IE_OK) return fail(ws);
@@ -480,7 +549,11 @@ static void flush_solve_timing(ie_handle h) {
     if (cudaEventQuery(r.b) != cudaSuccess) { cudaGetLastError(); keep.push_back(r); continue; }
     float ms = 0;
     cudaEventElapsedTime(&ms, r.a, r.b);
-    if (r.fp32) {
+    if (r.adj) {
+      h->t_adj_ms += ms;
+      h->adj_flops += r.flops;
+      h->adj_launches += 1;
+    } else if (r.fp32) {
       h->t_solve32_ms += ms;
       h->solve32_flops += r.flops;
       h->solve32_launches += 1;
@@ -508,12 +581,13 @@ static ie_status check_status(ie_handle h, cudaStream_t s) {
 
 // ------------------------------ inner operator G ----------------------------------------------
 // GV = sum_i w_i K_i^{-1} B V (Eq. linearsolve2). V columns at V + off[c] when d_off != null.
+// On the adjoint side (h->side = 1): GV = sum_i conj(w_i) K_i^{-H} B^H V.
 static ie_status apply_G_mixed(ie_handle h, int k, cplx* GV, int64_t ldg, cudaStream_t s);
 
 static ie_status apply_G_dev(ie_handle h, const cplx* V, int64_t ldv, const int64_t* d_off, int k,
                              cplx* GV, int64_t ldg, cudaStream_t s) {
   if (k <= 0) return IE_OK;
-  launch_spmv(h->P, make_double2(0, 0), make_double2(1, 0), V, ldv, d_off, k, h->BVw, h->n, s);
+  launch_spmv(h->pen(), make_double2(0, 0), make_double2(1, 0), V, ldv, d_off, k, h->BVw, h->n, s);
   if (h->precision == 1) return apply_G_mixed(h, k, GV, ldg, s);
   ie_handle_s::SolveRec rec;
   rec.a = h->get_event();
@@ -526,11 +600,18 @@ static ie_status apply_G_dev(ie_handle h, const cplx* V, int64_t ldv, const int6
     rec.flops = q * k * (8.0 * (fwd + bwd) + 12.0 * n);
     rec.bytes = q * n * (16.0 * (kl + kv + 1) + 4.0) + 16.0 * n * k * (1.0 + 3.0 * q);
     rec.fp32 = 0;
+    rec.adj = h->side;
   }
   cudaEventRecord(rec.a, s);
-  CK(launch_band_solve(h->q, h->n, h->kl, h->n_pad, h->L64, h->U64, h->piv, h->dinv, h->Tb, h->Hb,
-                       h->Uinvb, h->d_weights, h->BVw, h->n, k, h->Xp, h->n, h->n * (int64_t)h->kmax,
-                       h->status, s));
+  if (h->side) {
+    CK(launch_band_solve_adj(h->q, h->n, h->kl, h->n_pad, h->L64, h->Ut64, h->Uinvb, h->Madj64,
+                             h->Hb, h->d_wconj, h->BVw, h->n, k, h->Xp, h->n,
+                             h->n * (int64_t)h->kmax, h->status, s));
+  } else {
+    CK(launch_band_solve(h->q, h->n, h->kl, h->n_pad, h->L64, h->U64, h->piv, h->dinv, h->Tb,
+                         h->Hb, h->Uinvb, h->d_weights, h->BVw, h->n, k, h->Xp, h->n,
+                         h->n * (int64_t)h->kmax, h->status, s));
+  }
   cudaEventRecord(rec.b, s);
   h->pending.push_back(rec);
   launch_pole_sum(h->q, h->n, k, h->Xp, h->n, h->n * (int64_t)h->kmax, GV, ldg, s);
@@ -541,31 +622,41 @@ static ie_status apply_G_dev(ie_handle h, const cplx* V, int64_t ldv, const int6
 // Mixed precision (opts.precision = 1), B V already in h->BVw: per pole i,
 //   x_i = K~_i^{-1} BV (complex64 factors, FP32 solve), then refine_steps times
 //   x_i += K~_i^{-1} (BV - K_i x_i) with the residual in FP64; GV = sum_i w_i x_i.
+// The adjoint side uses K_i^H = conj(p_i) B^H - A^H and conj(w_i) throughout.
 static ie_status apply_G_mixed(ie_handle h, int k, cplx* GV, int64_t ldg, cudaStream_t s) {
   const int64_t n = h->n, ps = n * (int64_t)h->kmax;
   const double nn = (double)n, kl = h->kl, kv = h->kv, q = h->q;
   const double fwd = nn * kl - 0.5 * kl * (kl + 1), bwd = nn * kv - 0.5 * kv * (kv + 1);
   const double flops = q * k * (8.0 * (fwd + bwd) + 12.0 * nn);
+  const bool adj = h->side != 0;
   launch_to_c64(n, k, h->BVw, n, h->BV32, n, s);
   for (int it = 0; it <= h->refine; ++it) {
     if (it > 0)
-      launch_pole_residual(h->P, h->d_poles, h->q, k, h->BVw, n, h->Xp, n, ps, h->R32, n, ps, s);
+      launch_pole_residual(h->pen(), adj ? h->d_pconj : h->d_poles, h->q, k, h->BVw, n, h->Xp, n,
+                           ps, h->R32, n, ps, s);
     ie_handle_s::SolveRec rec;
     rec.a = h->get_event();
     rec.b = h->get_event();
     rec.flops = flops;
     rec.bytes = 0;
     rec.fp32 = 1;
+    rec.adj = adj;
     cudaEventRecord(rec.a, s);
-    CK(launch_band_solve32(h->q, n, h->kl, h->n_pad, h->L32, h->klp, h->U32, h->kv, h->piv,
-                           h->dinv32, h->T32, h->Hb, h->Ub32, h->d_weights,
-                           it == 0 ? h->BV32 : h->R32, n,
-                           it == 0 ? 0 : ps, k, h->Y32, n, ps, h->Xp, n, ps, it > 0 ? 1 : 0,
-                           h->status, s));
+    const float2* rhs = it == 0 ? h->BV32 : h->R32;
+    const int64_t rstride = it == 0 ? 0 : ps;
+    if (adj) {
+      CK(launch_band_solve_adj32(h->q, n, h->kl, h->n_pad, h->L32, h->klp, h->Ut32, h->Ub32,
+                                 h->Madj32, h->Hb, h->d_wconj, rhs, n, rstride, k, h->Y32, n, ps,
+                                 h->Xp, n, ps, it > 0 ? 1 : 0, h->status, s));
+    } else {
+      CK(launch_band_solve32(h->q, n, h->kl, h->n_pad, h->L32, h->klp, h->U32, h->kv, h->piv,
+                             h->dinv32, h->T32, h->Hb, h->Ub32, h->d_weights, rhs, n, rstride, k,
+                             h->Y32, n, ps, h->Xp, n, ps, it > 0 ? 1 : 0, h->status, s));
+    }
     cudaEventRecord(rec.b, s);
     h->pending.push_back(rec);
   }
-  launch_pole_wsum(h->q, n, k, h->Xp, n, ps, h->d_weights, GV, ldg, s);
+  launch_pole_wsum(h->q, n, k, h->Xp, n, ps, adj ? h->d_wconj : h->d_weights, GV, ldg, s);
   h->g_columns += k;
   return IE_OK;
 }
@@ -722,9 +813,10 @@ static ie_status hsrr_dev(ie_handle h, const cplx* U, int64_t ldu, int k, cudaSt
   launch_copy_cols(n, k, U, ldu, h->Vh, n, s);
   launch_orth_cgs2(n, k, h->Vh, n, seed, h->salt++, h->hbuf, h->scratch, h->d_flags, s);  // V
   const cplx one = make_double2(1, 0), zero = make_double2(0, 0);
-  launch_spmv(h->P, one, zero, h->Vh, n, nullptr, k, h->AVh, n, s);                       // AV
-  launch_spmv(h->P, zero, one, h->Vh, n, nullptr, k, h->BVh, n, s);                       // BV
-  launch_spmv(h->P, one, to_c(-h->sigma), h->Vh, n, nullptr, k, h->Wh, n, s);            // AV - sigma BV
+  const DiaDev& P = h->pen();
+  launch_spmv(P, one, zero, h->Vh, n, nullptr, k, h->AVh, n, s);                          // AV
+  launch_spmv(P, zero, one, h->Vh, n, nullptr, k, h->BVh, n, s);                          // BV
+  launch_spmv(P, one, to_c(-h->sig()), h->Vh, n, nullptr, k, h->Wh, n, s);               // AV - sigma BV
   launch_orth_cgs2(n, k, h->Wh, n, seed, h->salt++, h->hbuf, h->scratch, h->d_flags, s);  // W
   launch_gram(n, k, h->Wh, n, h->AVh, n, h->Ah, (cplx*)h->scratch, s);                    // W^H A V
   launch_gram(n, k, h->Wh, n, h->BVh, n, h->Bh, (cplx*)h->scratch, s);                    // W^H B V
@@ -745,18 +837,18 @@ static ie_status hsrr_dev(ie_handle h, const cplx* U, int64_t ldu, int k, cudaSt
   CK(cudaMemcpyAsync(h->d_lam, lamc.data(), sizeof(cplx) * k, cudaMemcpyHostToDevice, s));
   launch_gemm_small(n, k, h->Vh, n, h->Mq, h->Xh, n, s);                                  // x = V P_R V_R
   launch_normalize_cols(n, k, h->Xh, n, h->scratch, s);
-  launch_residual_norms(h->P, k, h->Xh, n, h->d_lam, h->d_rn, h->scratch, s);
+  launch_residual_norms(P, k, h->Xh, n, h->d_lam, h->d_rn, h->scratch, s);
   std::vector<double> rn(3 * k);
   CK(cudaMemcpyAsync(rn.data(), h->d_rn, sizeof(double) * 3 * k, cudaMemcpyDeviceToHost, s));
   CKS(check_status(h, s));
   e.resize(k);
   rho.resize(k);
-  const double scale_e = std::abs(h->center) + h->radius;
+  const double scale_e = std::abs(h->ctr()) + h->radius;
   for (int i = 0; i < k; ++i) {
     const bool fin = std::isfinite(lam[i].real()) && std::isfinite(lam[i].imag());
     const double r = std::sqrt(rn[3 * i]), bx = std::sqrt(rn[3 * i + 1]), xn = std::sqrt(rn[3 * i + 2]);
     e[i] = fin ? r / (scale_e * bx) : inf;
-    rho[i] = fin ? r / ((h->normA + std::abs(lam[i]) * h->normB) * xn) : inf;
+    rho[i] = fin ? r / ((h->nA() + std::abs(lam[i]) * h->nB()) * xn) : inf;
   }
   return IE_OK;
 }
@@ -794,15 +886,13 @@ extern "C" ie_status ie_hsrr(ie_handle h, const ie_complex* U_any, int64_t ldu, 
 
 // ------------------------------ drivers ----------------------------------------------------------
 static bool in_disk(ie_handle h, zc l) {
-  return std::isfinite(l.real()) && std::isfinite(l.imag()) && std::abs(l - h->center) < h->radius;
+  return std::isfinite(l.real()) && std::isfinite(l.imag()) && std::abs(l - h->ctr()) < h->radius;
 }
 
-extern "C" ie_status ie_solve(ie_handle h, const ie_complex* Y0_any, int64_t ldy0,
+// Alg. 1 / Alg. 2 on the handle's current side (the pencil (A, B), or its adjoint).
+static ie_status solve_driver(ie_handle h, const ie_complex* Y0_any, int64_t ldy0,
                               ie_complex* h_lambda, ie_complex* X_any, int64_t ldx, double* h_rho,
-                              double* h_e, int32_t* n_found, ie_stats* stats, void* stream) {
-  if (!h || !h_lambda || !X_any || !n_found || ldx < h->n) return IE_ERR_ARG;
-  if (Y0_any && ldy0 < h->n) return IE_ERR_ARG;
-  cudaStream_t s = (cudaStream_t)stream;
+                              double* h_e, int32_t* n_found, ie_stats* stats, cudaStream_t s) {
   const int k = h->kmax;
   const int64_t n = h->n;
   // starting block
@@ -889,7 +979,7 @@ extern "C" ie_status ie_solve(ie_handle h, const ie_complex* Y0_any, int64_t ldy
   std::iota(ord.begin(), ord.end(), 0);
   auto dist = [&](int i) {
     return (std::isfinite(lam[i].real()) && std::isfinite(lam[i].imag()))
-               ? std::abs(lam[i] - h->center)
+               ? std::abs(lam[i] - h->ctr())
                : std::numeric_limits<double>::infinity();
   };
   std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) {
@@ -916,6 +1006,137 @@ extern "C" ie_status ie_solve(ie_handle h, const ie_complex* Y0_any, int64_t ldy
   if (stats) *stats = S;
   (void)any_noconv;
   return converged ? IE_OK : IE_ERR_NOCONV;
+}
+
+extern "C" ie_status ie_solve(ie_handle h, const ie_complex* Y0_any, int64_t ldy0,
+                              ie_complex* h_lambda, ie_complex* X_any, int64_t ldx, double* h_rho,
+                              double* h_e, int32_t* n_found, ie_stats* stats, void* stream) {
+  if (!h || !h_lambda || !X_any || !n_found || ldx < h->n) return IE_ERR_ARG;
+  if (Y0_any && ldy0 < h->n) return IE_ERR_ARG;
+  h->side = 0;
+  return solve_driver(h, Y0_any, ldy0, h_lambda, X_any, ldx, h_rho, h_e, n_found, stats,
+                      (cudaStream_t)stream);
+}
+
+// ------------------------------ adjoint pencil --------------------------------------------------
+namespace {
+struct SideGuard {   // the adjoint side for the guard's lifetime
+  ie_handle h;
+  explicit SideGuard(ie_handle h_) : h(h_) { h->side = 1; }
+  ~SideGuard() { h->side = 0; }
+};
+}  // namespace
+
+extern "C" ie_status ie_apply_GH(ie_handle h, const ie_complex* V_any, int64_t ldv, int32_t k,
+                                 ie_complex* GV_any, int64_t ldgv, void* stream) {
+  if (!h || !h->adj || !V_any || !GV_any || k < 1 || k > h->kmax || ldv < h->n || ldgv < h->n)
+    return IE_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  SideGuard g(h);
+  const cplx* V;
+  CKS(stage_in(h, V_any, ldv, k, h->Yb, s, &V));
+  const bool gdev = is_device_ptr(GV_any);
+  cplx* G = gdev ? (cplx*)GV_any : h->Ub;
+  const int64_t ldG = gdev ? ldgv : h->n;
+  CKS(apply_G_dev(h, V, V == h->Yb ? h->n : ldv, nullptr, k, G, ldG, s));
+  if (!gdev) CKS(stage_out(h, G, ldG, k, GV_any, ldgv, s));
+  h->stats.g_columns = h->g_columns;
+  return check_status(h, s);
+}
+
+extern "C" ie_status ie_solve_left(ie_handle h, const ie_complex* h_lambda, int32_t nl,
+                                   const ie_complex* Y0_any, int64_t ldy0, ie_complex* Y_any,
+                                   int64_t ldy, ie_complex* h_lambda_left, double* h_rho_left,
+                                   ie_stats* stats, void* stream) {
+  if (!h || !h->adj || !h_lambda || !Y_any || nl < 1 || nl > h->kmax || ldy < h->n) return IE_ERR_ARG;
+  if (Y0_any && ldy0 < h->n) return IE_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int k = h->kmax;
+  const int64_t n = h->n;
+  std::vector<ie_complex> mu(k);
+  std::vector<double> rho(k);
+  int32_t nf = 0;
+  ie_status st;
+  {
+    SideGuard g(h);
+    // the driver leaves its ordered Ritz vectors in h->Wb (n x k)
+    st = solve_driver(h, Y0_any, ldy0, mu.data(), (ie_complex*)h->Wb, n, rho.data(), nullptr, &nf,
+                      stats, s);
+  }
+  if (st != IE_OK && st != IE_ERR_NOCONV) return st;
+  // pair each requested eigenvalue with the nearest conj(mu_j), one-to-one
+  std::vector<int> perm(nl, 0);
+  std::vector<char> used(k, 0);
+  bool paired = true;
+  for (int i = 0; i < nl; ++i) {
+    const zc li = to_z(h_lambda[i]);
+    int best = -1;
+    double bd = std::numeric_limits<double>::infinity();
+    for (int j = 0; j < k; ++j) {
+      const zc mj = std::conj(to_z(mu[j]));
+      if (!std::isfinite(mj.real()) || !std::isfinite(mj.imag())) continue;
+      const double d = std::abs(mj - li);
+      if (d < bd) { bd = d; best = j; }
+    }
+    if (best < 0) { paired = false; continue; }
+    if (used[best] || !(bd <= 1e-8 * std::max(std::abs(li), h->radius))) paired = false;
+    used[best] = 1;
+    perm[i] = best;
+    if (h_lambda_left) {
+      h_lambda_left[i].re = mu[best].re;
+      h_lambda_left[i].im = -mu[best].im;
+    }
+    if (h_rho_left) h_rho_left[i] = rho[best];
+  }
+  CK(cudaMemcpyAsync(h->d_perm, perm.data(), sizeof(int) * nl, cudaMemcpyHostToDevice, s));
+  const bool ydev = is_device_ptr(Y_any);
+  cplx* Yo = ydev ? (cplx*)Y_any : h->Ub;
+  const int64_t ldYo = ydev ? ldy : n;
+  launch_permute_cols(n, nl, h->Wb, n, h->d_perm, Yo, ldYo, s);
+  if (!ydev) CKS(stage_out(h, Yo, ldYo, nl, Y_any, ldy, s));
+  CKS(check_status(h, s));
+  if (stats) fill_solve_stats(h, stats);
+  if (st != IE_OK || !paired) return IE_ERR_NOCONV;
+  return IE_OK;
+}
+
+extern "C" ie_status ie_eig_sensitivity(ie_handle h, const ie_complex* X_any, int64_t ldx,
+                                        const ie_complex* Y_any, int64_t ldy, int32_t nf,
+                                        ie_complex alpha, ie_complex* S_any, int64_t lds,
+                                        const ie_complex* h_gbar, double* grad_any, void* stream) {
+  if (!h || !X_any || !Y_any || nf < 1 || nf > h->kmax || ldx < h->n || ldy < h->n) return IE_ERR_ARG;
+  if ((S_any && lds < h->n) || (grad_any && !h_gbar)) return IE_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int64_t n = h->n;
+  const cplx* X;
+  const cplx* Y;
+  CKS(stage_in(h, X_any, ldx, nf, h->Yb, s, &X));
+  CKS(stage_in(h, Y_any, ldy, nf, h->Ub, s, &Y));
+  const int64_t ldX = (X == h->Yb) ? n : ldx, ldY = (Y == h->Ub) ? n : ldy;
+  const bool sdev = S_any && is_device_ptr(S_any);
+  cplx* S = S_any ? (sdev ? (cplx*)S_any : h->Xh) : nullptr;
+  const int64_t ldS = sdev ? lds : n;
+  double* grad = nullptr;
+  cplx* gb = nullptr;
+  if (grad_any) {
+    if (is_device_ptr(grad_any)) {
+      grad = grad_any;
+    } else {
+      if (!h->d_grad) CK(h->alloc(&h->d_grad, (size_t)n));
+      grad = h->d_grad;
+    }
+    std::vector<cplx> g(nf);
+    for (int i = 0; i < nf; ++i) g[i] = make_double2(h_gbar[i].re, h_gbar[i].im);
+    CK(cudaMemcpyAsync(h->betaq, g.data(), sizeof(cplx) * nf, cudaMemcpyHostToDevice, s));
+    CK(cudaStreamSynchronize(s));
+    gb = h->betaq;
+  }
+  launch_sensitivity(h->P, nf, X, ldX, Y, ldY, make_double2(alpha.re, alpha.im), h->Wb, h->alpha,
+                     S, ldS, gb, grad, s);
+  if (S_any && !sdev) CKS(stage_out(h, S, ldS, nf, S_any, lds, s));
+  if (grad_any && grad != grad_any)
+    CK(cudaMemcpyAsync(grad_any, grad, sizeof(double) * n, cudaMemcpyDeviceToHost, s));
+  return check_status(h, s);
 }
 
 // ------------------------------ introspection -----------------------------------------------
@@ -965,6 +1186,9 @@ static void fill_solve_stats(ie_handle h, ie_stats* out) {
   out->solve32_launches = h->solve32_launches;
   out->t_solve32_ms = h->t_solve32_ms;
   out->solve32_flops = h->solve32_flops;
+  out->adj_launches = h->adj_launches;
+  out->t_adj_ms = h->t_adj_ms;
+  out->adj_flops = h->adj_flops;
 }
 
 extern "C" ie_status ie_get_stats(ie_handle h, ie_stats* out) {

@@ -199,6 +199,36 @@ void launch_random_block(int64_t n, int k, cplx* X, int64_t ldx, uint64_t seed, 
 void launch_copy_cols(int64_t n, int k, const cplx* X, int64_t ldx, cplx* Y, int64_t ldy,
                       cudaStream_t s);
 
+// ---- adjoint pencil and sensitivities (ie_adjoint.cu) ----
+// (A^H, B^H) in DIA form into AH, BH (ndiag * n each); *PH describes them.
+void launch_dia_adjoint(const DiaDev& P, cplx* AH, cplx* BH, DiaDev* PH, cudaStream_t s);
+// U by rows from the band LU: row j's U(j, j+1..j+2kl) at Ut + (pole*n_pad + j)*2kl.
+void launch_u_rows(int q, int64_t n, int64_t n_pad, int kl, int ldab, const cplx* AB, cplx* Ut64,
+                   float2* Ut32, cudaStream_t s);
+// Per (pole, 8-row panel): the 16x24 transform of the conjugate-transpose L sweep on the
+// members Hb (complex128 into M64; complex64 copy when M32 != null).
+void launch_adj_transforms(int q, int64_t n, int64_t n_pad, int kl, int ldab, const cplx* AB,
+                           const int* piv, const int* Hb, cplx* M64, float2* M32, cudaStream_t s);
+// Xp[i] = conj(w_i) K_i^{-H} RHS for all q poles (complex128 factors).
+cudaError_t launch_band_solve_adj(int q, int64_t n, int kl, int64_t n_pad, const cplx* L64,
+                                  const cplx* Ut64, const cplx* Ub, const cplx* M64, const int* Hb,
+                                  const cplx* d_wconj, const cplx* RHS, int64_t ldr, int k,
+                                  cplx* Xp, int64_t ldx, int64_t xstride, int* status,
+                                  cudaStream_t s);
+// complex64 factors, FP32 solve: X (FP64, per pole) = K~_i^{-H} RHS_i (accumulate = 0) or +=.
+cudaError_t launch_band_solve_adj32(int q, int64_t n, int kl, int64_t n_pad, const float2* L32,
+                                    int64_t ldl, const float2* Ut32, const float2* Ui32,
+                                    const float2* M32, const int* Hb, const cplx* d_wconj,
+                                    const float2* RHS, int64_t ldr, int64_t rstride, int k,
+                                    float2* Y32, int64_t ldy, int64_t ystride, cplx* X,
+                                    int64_t ldx, int64_t xstride, int accumulate, int* status,
+                                    cudaStream_t s);
+// den_i = y_i^H B x_i (BX: n x nf scratch); S[j, i] = alpha conj(y_i[j]) x_i[j] / den_i
+// (S nullable); grad[j] = Re sum_i conj(gbar_i) S[j, i] (grad nullable; gbar device).
+void launch_sensitivity(const DiaDev& P, int nf, const cplx* X, int64_t ldx, const cplx* Y,
+                        int64_t ldy, cplx alpha, cplx* BX, cplx* den, cplx* S, int64_t lds,
+                        const cplx* gbar, double* grad, cudaStream_t s);
+
 // Read-only view of a handle's factorisation (defined in ie_capi.cu).
 struct IeFactorsView {
   int dev;

@@ -38,7 +38,7 @@ class ie_opts(C.Structure):
                 ("max_outer", C.c_int32), ("tau_g", C.c_double), ("tau", C.c_double),
                 ("gmres_tol", C.c_double), ("sigma_is_center", C.c_int32),
                 ("sigma_re", C.c_double), ("sigma_im", C.c_double), ("seed", C.c_uint64),
-                ("precision", C.c_int32), ("refine_steps", C.c_int32)]
+                ("precision", C.c_int32), ("refine_steps", C.c_int32), ("adjoint", C.c_int32)]
 
 
 class ie_stats(C.Structure):
@@ -50,7 +50,8 @@ class ie_stats(C.Structure):
                 ("t_solve_ms", C.c_double), ("solve_flops", C.c_double),
                 ("solve_bytes", C.c_double), ("kernel_launches", C.c_int64),
                 ("solve32_launches", C.c_int64), ("t_solve32_ms", C.c_double),
-                ("solve32_flops", C.c_double)]
+                ("solve32_flops", C.c_double), ("adj_launches", C.c_int64),
+                ("t_adj_ms", C.c_double), ("adj_flops", C.c_double)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -58,7 +59,8 @@ class ie_stats(C.Structure):
 
 EXPORTS = ["ie_opts_default", "ie_create", "ie_destroy", "ie_status_str", "ie_filter_apply",
            "ie_apply_G", "ie_hsrr", "ie_solve", "ie_spmv", "ie_get_coeffs", "ie_get_factor",
-           "ie_get_stats", "ie_apply_G_static"]
+           "ie_get_stats", "ie_apply_G_static", "ie_apply_GH", "ie_solve_left",
+           "ie_eig_sensitivity"]
 
 _lib = None
 _vp, _i32, _i64, _dp = C.c_void_p, C.c_int32, C.c_int64, C.POINTER(C.c_double)
@@ -89,6 +91,11 @@ def load():
     L.ie_get_factor.argtypes = [_vp, _i32, _vp, _vp, C.POINTER(_i32), C.POINTER(_i32)]
     L.ie_get_stats.argtypes = [_vp, C.POINTER(ie_stats)]
     L.ie_apply_G_static.argtypes = [_vp, _vp, _i64, _i32, _vp, _i64, _vp]
+    L.ie_apply_GH.argtypes = [_vp, _vp, _i64, _i32, _vp, _i64, _vp]
+    L.ie_solve_left.argtypes = [_vp, _vp, _i32, _vp, _i64, _vp, _i64, _vp, _vp,
+                                C.POINTER(ie_stats), _vp]
+    L.ie_eig_sensitivity.argtypes = [_vp, _vp, _i64, _vp, _i64, _i32, ie_complex, _vp, _i64, _vp,
+                                     _vp, _vp]
     for f in EXPORTS:
         if f not in ("ie_opts_default", "ie_status_str"):
             getattr(L, f).restype = C.c_int
@@ -232,6 +239,43 @@ def ie_solve(h, Y0, X, k, stream=None):
     st = load().ie_solve(h, p0, ld0 if Y0 is not None else 0, _vec(lam), px, ldx, _vec(rho),
                          _vec(e), C.byref(nf), C.byref(stt), _stream(stream))
     return st, lam, rho, e, nf.value, stt.as_dict()
+
+
+def ie_apply_GH(h, V, GV, stream=None):
+    """GV = sum_i conj(w_i) K_i^{-H} B^H V (handles created with opts.adjoint = 1)."""
+    pv, ldv, n, k = _block(V)
+    pg, ldg, _, _ = _block(GV)
+    return load().ie_apply_GH(h, pv, ldv, k, pg, ldg, _stream(stream))
+
+
+def ie_solve_left(h, lam, Y, Y0=None, stream=None):
+    """Left eigenvectors for the eigenvalues `lam` (nl,) into the first nl columns of Y.
+    Returns (status, lambda_left (nl,), rho_left (nl,), stats dict)."""
+    lam = np.ascontiguousarray(np.asarray(lam, dtype=np.complex128))
+    nl = len(lam)
+    p0, ld0, _, _ = _block(Y0)
+    py, ldy, _, _ = _block(Y)
+    ll = np.zeros(nl, dtype=np.complex128)
+    rl = np.zeros(nl)
+    stt = ie_stats()
+    st = load().ie_solve_left(h, _vec(lam), nl, p0, ld0 if Y0 is not None else 0, py, ldy,
+                              _vec(ll), _vec(rl), C.byref(stt), _stream(stream))
+    return st, ll, rl, stt.as_dict()
+
+
+def ie_eig_sensitivity(h, X, Y, alpha=1j, S=None, gbar=None, grad=None, stream=None):
+    """S[j, i] = alpha conj(Y[j, i]) X[j, i] / (Y_i^H B X_i) into S (n x nf) and
+    grad[j] = Re sum_i conj(gbar_i) S[j, i] into grad (n doubles); either may be None."""
+    px, ldx, n, nf = _block(X)
+    py, ldy, _, _ = _block(Y)
+    ps, lds, _, _ = _block(S)
+    gb = None
+    if gbar is not None:
+        gb = np.ascontiguousarray(np.asarray(gbar, dtype=np.complex128))
+    a = complex(alpha)
+    return load().ie_eig_sensitivity(h, px, ldx, py, ldy, nf, ie_complex(a.real, a.imag), ps,
+                                     lds if S is not None else 0, _vec(gb), _vec(grad),
+                                     _stream(stream))
 
 
 def ie_get_coeffs(h, p, q):

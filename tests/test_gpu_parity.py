@@ -51,7 +51,8 @@ class Case:
         self.n = self.pen.n
         self.A, self.B = opencil.pencil_matrices(self.pen)
         opts = ie.ie_opts_default(k=w["k"], driver=w.get("driver", 1), seed=0)
-        for key in ("m_max", "max_outer", "gmres_tol", "precision", "refine_steps", "tau"):
+        for key in ("m_max", "max_outer", "gmres_tol", "precision", "refine_steps", "tau",
+                    "adjoint"):
             if key in w:
                 setattr(opts, key, w[key])
         self.Ad = torch.from_numpy(self.pen.A_dia).to(DEV)

@@ -123,3 +123,42 @@ def test_c4_mixed_precision_solve(ie):
         assert stats["solve32_launches"] > 0 and stats["solve_launches"] == 0
     finally:
         c.close()
+
+
+def test_c2_left_eigenvectors_and_sensitivities(ie):
+    """The bench workload (m = 256) with the mixed-precision adjoint handle: right solve, left
+    solve of the 40 eigenvalues in D, then the sensitivities to gamma. Checked by properties
+    that hold at any size: every left pair's residual for (A^H, B^H) recomputed on the CPU is
+    <= 1e-10, the paired eigenvalues agree within their residual bounds, and S at 64 seeded
+    nodes equals the oracle's formula evaluated on the returned X and Y."""
+    from oracle import adjoint as oadj, pencil as opencil
+    c = Case(ie, "c2_m256", m_max=150, precision=1, adjoint=1)
+    try:
+        k = c.w["k"]
+        Y0 = ie_inputs.orthonormal_random_block(c.n, k, seed=c.w["seed"])
+        Xd = dzeros(c.n, k)
+        st, lam, rho, e, nf, _ = ie.ie_solve(c.h, dblock(Y0), Xd, k)
+        assert st == ie.IE_OK and nf == 40
+        lam, rho = np.asarray(lam[:nf]), np.asarray(rho[:nf])
+        Yd = dzeros(c.n, k)
+        st, ll, rl, stats = ie.ie_solve_left(c.h, lam, Yd)
+        assert st == ie.IE_OK, ie.ie_status_str(st)
+        assert stats["adj_launches"] > 0
+        AH, BH = oadj.adjoint_pencil(c.A, c.B)
+        nAH, nBH = opencil.norm1(AH), opencil.norm1(BH)
+        Y = Yd.cpu().numpy()[:, :nf]
+        _, rho2 = ohsrr.residuals(AH, BH, np.conj(lam), Y, np.conj(c.w["center"]), c.w["radius"],
+                                  nAH, nBH)
+        assert np.all(rho2 <= 1e-10), rho2.max()
+        scale = (opencil.norm1(c.A) + np.abs(lam) * opencil.norm1(c.B)) / np.abs(lam)
+        assert np.all(np.abs(ll - lam) / np.abs(lam) <= 4 * (rho + rl) * scale + 1e-13)
+        Sd = dzeros(c.n, nf)
+        assert ie.ie_eig_sensitivity(c.h, Xd[:, :nf], Yd[:, :nf], 1j, Sd) == ie.IE_OK
+        nodes = np.random.default_rng(5).choice(c.n, size=64, replace=False)
+        X = Xd.cpu().numpy()[:, :nf]
+        Sref = oadj.diag_sensitivity(c.B, X, Y, alpha=1j)
+        S = Sd.cpu().numpy()
+        err = np.abs(S[nodes] - Sref[nodes]) / np.abs(Sref[nodes]).max(axis=0)[None, :]
+        assert err.max() < 1e-12, err.max()
+    finally:
+        c.close()
