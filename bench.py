@@ -49,9 +49,10 @@ def parse():
     ap.add_argument("--mixed", type=int, default=1,
                     help="1 (with --precision 0): also report the mixed-precision path on the same "
                          "workload (throughput and time to all eigenpairs at the same residual)")
-    ap.add_argument("--sens", type=int, default=1,
+    ap.add_argument("--sens", type=int, default=1, choices=[0, 1, 2],
                     help="1: also time left eigenvectors + eigenvalue sensitivities (adjoint "
-                         "pencil) and the conjugate-transpose band-solve kernel")
+                         "pencil) and the conjugate-transpose band-solve kernel; 2: only that "
+                         "kernel")
     ap.add_argument("--precision", type=int, default=0, choices=[0, 1],
                     help="0: complex128 factors and solves; 1: complex64 factors, FP32 solves, "
                          "FP64 refinement")
@@ -307,7 +308,8 @@ def run_native(args):
 
     sens = None
     if args.sens and rank == 0:
-        sens = time_sensitivities(ie, w, pen, A_d, B_d, device, stream, Xd)
+        sens = time_sensitivities(ie, w, pen, A_d, B_d, device, stream, Xd,
+                                  kernel_only=args.sens == 2)
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -361,7 +363,7 @@ def run_native(args):
         dist.destroy_process_group()
 
 
-def time_sensitivities(ie, w, pen, A_d, B_d, device, stream, Xd):
+def time_sensitivities(ie, w, pen, A_d, B_d, device, stream, Xd, kernel_only=False):
     """Eigenvalue derivatives on the same workload: right eigenpairs (ie_solve), left
     eigenvectors by the adjoint pencil (ie_solve_left) and the gradient of the seeded loss
     J = sum_i w_i Re(lambda_i), w_i ~ U(0, 1), with respect to gamma at every grid node
@@ -373,12 +375,48 @@ def time_sensitivities(ie, w, pen, A_d, B_d, device, stream, Xd):
     n, k, p, q = pen.n, w["k"], w["p"], w["q"]
     out = {"loss": "J = sum_i w_i Re(lambda_i) over the eigenvalues in D, w_i ~ U(0,1) (seed 5); "
                    "dJ/dgamma at all n nodes"}
+    if not kernel_only:
+        time_left_and_gradient(ie, w, pen, A_d, B_d, device, stream, Xd, out)
+    # the complex128 conjugate-transpose solve kernel, timed by the library per launch
+    o64 = ie.ie_opts_default(k=k, m_max=150, precision=0, adjoint=1)
+    st, h = ie.ie_create(n, pen.offsets, A_d, B_d, w["center"], w["radius"], p, q, o64, stream)
+    if st != ie.IE_OK:
+        out["band_solve_adj_c128"] = {"error": ie.ie_status_str(st)}
+        return out
+    V = torch.from_numpy(np.ascontiguousarray(ie_inputs.random_block(n, k, seed=3).T)).to(device).T
+    GV = torch.zeros((k, n), dtype=torch.complex128, device=device).T
+    for _ in range(2):   # warm-up
+        ie.ie_apply_GH(h, V, GV, stream)
+    torch.cuda.synchronize()
+    _, a0 = ie.ie_get_stats(h)
+    for _ in range(3):
+        ie.ie_apply_GH(h, V, GV, stream)
+    torch.cuda.synchronize()
+    _, a1 = ie.ie_get_stats(h)
+    la = a1["adj_launches"] - a0["adj_launches"]
+    ms = a1["t_adj_ms"] - a0["t_adj_ms"]
+    fl = a1["adj_flops"] - a0["adj_flops"]
+    ach = fl / (ms / 1e3) / 1e12 if ms > 0 else None
+    out["band_solve_adj_c128"] = {"kernel": "band_solve_adj_kernel", "k": k, "launches": la,
+                                  "avg_launch_ms": ms / la if la else None,
+                                  "achieved_tflops": ach, "peak_tflops": FP64_PEAK_TFLOPS,
+                                  "frac": ach / FP64_PEAK_TFLOPS if ach else None}
+    ie.ie_destroy(h)
+    return out
+
+
+def time_left_and_gradient(ie, w, pen, A_d, B_d, device, stream, Xd, out):
+    import torch
+
+    import ie_inputs
+    n, k, p, q = pen.n, w["k"], w["p"], w["q"]
     om = ie.ie_opts_default(k=k, m_max=150, precision=1, adjoint=1)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     st, h = ie.ie_create(n, pen.offsets, A_d, B_d, w["center"], w["radius"], p, q, om, stream)
     if st != ie.IE_OK:
-        return {"error": ie.ie_status_str(st)}
+        out["error"] = ie.ie_status_str(st)
+        return
     torch.cuda.synchronize()
     out["create_s"] = time.perf_counter() - t0
     Y0 = ie_inputs.orthonormal_random_block(n, k, seed=w["seed"])
@@ -409,32 +447,6 @@ def time_sensitivities(ie, w, pen, A_d, B_d, device, stream, Xd):
                 "gradient_ms": e0.elapsed_time(e1),
                 "grad_norm": float(torch.linalg.vector_norm(grad).item())})
     ie.ie_destroy(h)
-    # the complex128 conjugate-transpose solve kernel, timed by the library per launch
-    o64 = ie.ie_opts_default(k=k, m_max=150, precision=0, adjoint=1)
-    st, h = ie.ie_create(n, pen.offsets, A_d, B_d, w["center"], w["radius"], p, q, o64, stream)
-    if st != ie.IE_OK:
-        out["band_solve_adj_c128"] = {"error": ie.ie_status_str(st)}
-        return out
-    V = torch.from_numpy(np.ascontiguousarray(ie_inputs.random_block(n, k, seed=3).T)).to(device).T
-    GV = torch.zeros((k, n), dtype=torch.complex128, device=device).T
-    for _ in range(2):   # warm-up
-        ie.ie_apply_GH(h, V, GV, stream)
-    torch.cuda.synchronize()
-    _, a0 = ie.ie_get_stats(h)
-    for _ in range(3):
-        ie.ie_apply_GH(h, V, GV, stream)
-    torch.cuda.synchronize()
-    _, a1 = ie.ie_get_stats(h)
-    la = a1["adj_launches"] - a0["adj_launches"]
-    ms = a1["t_adj_ms"] - a0["t_adj_ms"]
-    fl = a1["adj_flops"] - a0["adj_flops"]
-    ach = fl / (ms / 1e3) / 1e12 if ms > 0 else None
-    out["band_solve_adj_c128"] = {"kernel": "band_solve_adj_kernel", "k": k, "launches": la,
-                                  "avg_launch_ms": ms / la if la else None,
-                                  "achieved_tflops": ach, "peak_tflops": FP64_PEAK_TFLOPS,
-                                  "frac": ach / FP64_PEAK_TFLOPS if ach else None}
-    ie.ie_destroy(h)
-    return out
 
 
 # ------------------------------------------------------------------ CPU oracle
