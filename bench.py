@@ -49,6 +49,9 @@ def parse():
     ap.add_argument("--mixed", type=int, default=1,
                     help="1 (with --precision 0): also report the mixed-precision path on the same "
                          "workload (throughput and time to all eigenpairs at the same residual)")
+    ap.add_argument("--batch", type=int, default=1,
+                    help="1: also time the batched solver on the seeded 12-problem mix "
+                         "(sequential ie_solve vs ie_solve_batch)")
     ap.add_argument("--sens", type=int, default=1, choices=[0, 1, 2],
                     help="1: also time left eigenvectors + eigenvalue sensitivities (adjoint "
                          "pencil) and the conjugate-transpose band-solve kernel; 2: only that "
@@ -306,6 +309,10 @@ def run_native(args):
                                     "peak_tflops": FP32_PEAK_TFLOPS},
                  "time_to_all_eigenpairs": time_solves(1) if args.solve else None}
 
+    batch = None
+    if args.batch and rank == 0:
+        batch = time_batch(ie, device, stream)
+
     sens = None
     if args.sens and rank == 0:
         sens = time_sensitivities(ie, w, pen, A_d, B_d, device, stream, Xd,
@@ -354,6 +361,7 @@ def run_native(args):
             "time_to_all_eigenpairs": solves,
             "mixed_precision": mixed,
             "sensitivities": sens,
+            "batch": batch,
             "e2e": e2e,
             "clocks": clk.summary(),
             "cpu_baseline": cpu,
@@ -361,6 +369,72 @@ def run_native(args):
         print(json.dumps(line))
     if dist is not None:
         dist.destroy_process_group()
+
+
+def time_batch(ie, device, stream, workers=12):
+    """The seeded mix of 12 independent problems (grids 64..192, 1-2 disks per pencil, k 16..32,
+    q 4..8, p 4..8; tests/golden/workloads.json b*), complex128, Alg. 1: every problem solved
+    alone with ie_solve one after another, against all of them through ie_solve_batch
+    (one host worker and one stream per problem). Factorisations are done before and reported
+    apart. One untimed batch run first lets the launch-shape tuner settle for both timings."""
+    import torch
+
+    import ie_inputs
+    names = ie_inputs.batch_workload_names()
+    probs, hs, refs = [], [], []
+    t_create = 0.0
+    for nm in names:
+        w = ie_inputs.load_workload(nm)
+        pen = ie_inputs.make_pencil(w["m"], w["seed"])
+        A_d = torch.from_numpy(pen.A_dia).to(device)
+        B_d = torch.from_numpy(pen.B_dia).to(device)
+        o = ie.ie_opts_default(k=w["k"], m_max=150, driver=w["driver"])
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        st, h = ie.ie_create(pen.n, pen.offsets, A_d, B_d, w["center"], w["radius"], w["p"],
+                             w["q"], o, stream)
+        torch.cuda.synchronize()
+        t_create += time.perf_counter() - t0
+        if st != ie.IE_OK:
+            for hh in hs:
+                ie.ie_destroy(hh)
+            return {"error": f"{nm}: {ie.ie_status_str(st)}"}
+        hs.append(h)
+        Y0 = ie_inputs.orthonormal_random_block(pen.n, w["k"], seed=w["seed"])
+        Y0d = torch.from_numpy(np.ascontiguousarray(Y0.T)).to(device).T
+        X = torch.zeros((w["k"], pen.n), dtype=torch.complex128, device=device).T
+        refs.append(np.array(w["eig_in_disk_re"]) + 1j * np.array(w["eig_in_disk_im"]))
+        probs.append((h, Y0d, X, w["k"]))
+    ie.ie_solve_batch(probs, max_workers=workers)          # warm-up (tuner)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    seq = []
+    for (h, Y0d, X, k) in probs:
+        st, lam, rho, e, nf, _ = ie.ie_solve(h, Y0d, X, k, stream)
+        seq.append((st, lam[:nf].copy(), nf))
+    torch.cuda.synchronize()
+    t_seq = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    stb, res = ie.ie_solve_batch(probs, max_workers=workers)
+    torch.cuda.synchronize()
+    t_bat = time.perf_counter() - t0
+    same = all(r["n_found"] == s_[2] and np.allclose(r["lam"][:s_[2]], s_[1], rtol=1e-12, atol=0)
+               for r, s_ in zip(res, seq))
+    errs = []
+    for r, ref in zip(res, refs):
+        got = r["lam"][: r["n_found"]]
+        if len(got) == len(ref) and len(got):
+            errs.append(float(np.max(np.min(np.abs(got[:, None] - ref[None, :]), axis=1) / np.abs(got))))
+    for h in hs:
+        ie.ie_destroy(h)
+    return {"problems": len(names), "workers": workers, "create_s_total": t_create,
+            "sequential_s": t_seq, "batched_s": t_bat,
+            "problems_per_s_sequential": len(names) / t_seq,
+            "problems_per_s_batched": len(names) / t_bat, "speedup": t_seq / t_bat,
+            "status": ie.ie_status_str(stb), "same_as_sequential": bool(same),
+            "n_found": [r["n_found"] for r in res],
+            "n_in_disk_reference": [len(x) for x in refs],
+            "max_rel_err_vs_reference": max(errs) if errs else None}
 
 
 def time_sensitivities(ie, w, pen, A_d, B_d, device, stream, Xd, kernel_only=False):

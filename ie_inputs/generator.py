@@ -133,3 +133,50 @@ def load_workload(name: str) -> dict:
     w = dict(w)
     w["center"] = complex(w["center_re"], w["center_im"])
     return w
+
+
+def closed_form_spectrum(m: int) -> np.ndarray:
+    """Eigenvalues of the constant-coefficient part of A (-Laplace + (3, 2) . grad, central
+    differences, h = 1/(m+1)): (2/h^2)[2 - sqrt(1-(3h/2)^2) cos(j pi h) - sqrt(1-h^2) cos(k pi h)],
+    j, k = 1..m (each 1D factor is a tridiagonal Toeplitz matrix). Real, ascending. Used only
+    to place disks of the batch workload."""
+    h = 1.0 / (m + 1)
+    j = np.arange(1, m + 1)
+    ax = np.sqrt(1.0 - (1.5 * h) ** 2) * np.cos(j * np.pi * h)
+    ay = np.sqrt(1.0 - h ** 2) * np.cos(j * np.pi * h)
+    lam = (2.0 / h ** 2) * (2.0 - ax[:, None] - ay[None, :])
+    return np.sort(lam.ravel())
+
+
+BATCH_GRIDS = (64, 96, 128, 160, 192)
+
+
+def batch_problems(count: int = 12, seed: int = 0, grids=BATCH_GRIDS) -> list[dict]:
+    """Recipe of a seeded mix of independent problems (pencils and disks) for the batched
+    solver. Pencil j has grid grids[j mod len(grids)] and pencil seed 100 + j; it gets 1 or 2
+    disks. Disk d of a pencil: N = n_in in {6, 10, 16} eigenvalues with block width
+    k = 16, 24, 32, q in {4, 6, 8}, p in {4, 8}, driver 1. Its centre is placed near the
+    closed-form eigenvalue at the fraction proxy_frac = 1/4 + d/16 of the sorted spectrum (away
+    from the cluster at the middle of the 2D spectrum); tests/golden/make_golden.py fixes the
+    exact centre and radius from the oracle's eigenvalues and stores them in workloads.json
+    under `name`. Draws from PCG64(seed), independent of the pencils' own draws."""
+    g = _rng(seed)
+    out = []
+    j = 0
+    while len(out) < count:
+        m = int(grids[j % len(grids)])
+        ndisk = 1 + int(g.integers(0, 2))
+        for d in range(ndisk):
+            if len(out) == count:
+                break
+            N = int(g.choice([6, 10, 16]))
+            out.append({"name": f"b{len(out)}_m{m}_d{d}", "m": m, "seed": 100 + j,
+                        "k": {6: 16, 10: 24, 16: 32}[N], "q": int(g.choice([4, 6, 8])),
+                        "p": int(g.choice([4, 8])), "n_in": N, "driver": 1,
+                        "proxy_frac": 0.25 + d / 16.0})
+        j += 1
+    return out
+
+
+def batch_workload_names(count: int = 12, seed: int = 0) -> list[str]:
+    return [b["name"] for b in batch_problems(count, seed)]

@@ -264,6 +264,36 @@ ie_status ie_eig_sensitivity(ie_handle h, const ie_complex* X_any, int64_t ldx,
                              ie_complex* S_any, int64_t lds, const ie_complex* h_gbar,
                              double* grad_any, void* stream);
 
+/* ---------------------------------------------------------------------------------------
+ * Batched solves: many independent problems (pencils, or disks of one pencil) at once. The
+ * paper notes that disks are independent problems (Sec. 1); small problems leave most of the
+ * GPU idle during their sequential Arnoldi steps and host-side tests, so running their drivers
+ * concurrently fills it. */
+typedef struct {
+  ie_handle h;                 /* the problem; every item needs its own handle */
+  const ie_complex* Y0_any;    /* n x opts.k starting block, or NULL (seeded random) */
+  int64_t ldy0;
+  ie_complex* h_lambda;        /* out: opts.k eigenvalues (host), ordered as by ie_solve */
+  ie_complex* X_any;           /* out: n x opts.k eigenvectors, leading dimension ldx */
+  int64_t ldx;
+  double* h_rho;               /* out, nullable: opts.k residuals rho (host) */
+  double* h_e;                 /* out, nullable: opts.k errors e (host) */
+  void* stream;                /* stream for this item's work; NULL: the library makes a
+                                  non-blocking stream for the call and destroys it after */
+  int32_t n_found;             /* out */
+  int32_t status;              /* out: the item's ie_status */
+  ie_stats stats;              /* out */
+} ie_batch_item;
+
+/* ie_solve_batch: ie_solve for nb items concurrently. max_workers host threads (0: min(nb, 16))
+ * each take the next item, make its handle's device current and run the item's driver
+ * (opts.driver of its handle) on the item's stream. Every item's outputs equal those of
+ * ie_solve on its handle alone. Returns IE_ERR_ARG for nb < 1, a NULL item field that ie_solve
+ * requires, or two items sharing a handle (nothing runs); otherwise IE_OK if every item
+ * returned IE_OK, else the first non-OK item status in item order (all items still run).
+ * Not in the paper. */
+ie_status ie_solve_batch(ie_batch_item* items, int32_t nb, int32_t max_workers);
+
 #ifdef __cplusplus
 }
 #endif

@@ -473,7 +473,7 @@ template <typename CT, int NC, int SPT, int REGS>
 static cudaError_t launch_adj_r(const AdjArgsT<CT>& a, int q, int threads, size_t smem,
                                 cudaStream_t s) {
   auto kfn = band_solve_adj_kernel<CT, NC, SPT, REGS>;
-  cudaError_t e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = ie_smem_optin((const void*)kfn);
   if (e != cudaSuccess) return e;
   int blocks = 0;
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, kfn, threads, smem);

@@ -297,8 +297,7 @@ cudaError_t launch_band_lu(int q, int64_t n, int kl, int ldab, int64_t n_pad, cp
   if (P < 1) P = 1;
   int nown_max = (kv + P - 1) / P + 1;
   size_t smem = (size_t)(2 * (kl + 1) + 2 * nown_max) * sizeof(cplx);
-  if (smem > 48 * 1024)
-    cudaFuncSetAttribute(band_lu_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (smem > 48 * 1024) ie_smem_optin((const void*)band_lu_kernel);
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, band_lu_kernel, 512, smem);
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
   while ((int64_t)P * q > (int64_t)per_sm * sms && P > 1) {

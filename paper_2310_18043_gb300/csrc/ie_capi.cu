@@ -7,7 +7,10 @@
 #include <complex>
 #include <cstring>
 #include <limits>
+#include <atomic>
 #include <numeric>
+#include <set>
+#include <thread>
 #include <vector>
 
 #include "ie_internal.cuh"
@@ -1016,6 +1019,61 @@ extern "C" ie_status ie_solve(ie_handle h, const ie_complex* Y0_any, int64_t ldy
   h->side = 0;
   return solve_driver(h, Y0_any, ldy0, h_lambda, X_any, ldx, h_rho, h_e, n_found, stats,
                       (cudaStream_t)stream);
+}
+
+// ------------------------------ batched solves ---------------------------------------------------
+// A pool of host threads, each running whole drivers of the items it takes; item work goes to
+// one stream per item, so kernels and host round trips of different problems overlap.
+extern "C" ie_status ie_solve_batch(ie_batch_item* items, int32_t nb, int32_t max_workers) {
+  if (!items || nb < 1) return IE_ERR_ARG;
+  std::set<ie_handle> seen;
+  for (int i = 0; i < nb; ++i) {
+    const ie_batch_item& it = items[i];
+    if (!it.h || !it.h_lambda || !it.X_any || it.ldx < it.h->n) return IE_ERR_ARG;
+    if (it.Y0_any && it.ldy0 < it.h->n) return IE_ERR_ARG;
+    if (!seen.insert(it.h).second) return IE_ERR_ARG;
+  }
+  int workers = max_workers > 0 ? max_workers : std::min(nb, 16);
+  workers = std::min(workers, (int)nb);
+  std::atomic<int> next{0};
+  auto work = [&]() {
+    for (int i = next.fetch_add(1); i < nb; i = next.fetch_add(1)) {
+      ie_batch_item& it = items[i];
+      ie_handle h = it.h;
+      if (cudaSetDevice(h->dev) != cudaSuccess) { it.status = IE_ERR_CUDA; continue; }
+      cudaStream_t s = (cudaStream_t)it.stream;
+      bool own = false;
+      if (!s) {
+        if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
+          it.status = IE_ERR_CUDA;
+          continue;
+        }
+        own = true;
+      }
+      h->side = 0;
+      int32_t nf = 0;
+      ie_stats st{};
+      it.status = solve_driver(h, it.Y0_any, it.ldy0, it.h_lambda, it.X_any, it.ldx, it.h_rho,
+                               it.h_e, &nf, &st, s);
+      it.n_found = nf;
+      it.stats = st;
+      if (own) {
+        cudaStreamSynchronize(s);
+        cudaStreamDestroy(s);
+      }
+    }
+  };
+  if (workers == 1) {
+    work();
+  } else {
+    std::vector<std::thread> pool;
+    pool.reserve(workers);
+    for (int w = 0; w < workers; ++w) pool.emplace_back(work);
+    for (auto& t : pool) t.join();
+  }
+  for (int i = 0; i < nb; ++i)
+    if (items[i].status != IE_OK) return (ie_status)items[i].status;
+  return IE_OK;
 }
 
 // ------------------------------ adjoint pencil --------------------------------------------------

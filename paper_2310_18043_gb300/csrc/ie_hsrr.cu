@@ -478,8 +478,7 @@ cudaError_t launch_qz(int k, cplx* Ah, cplx* Bh, cplx* Z, cplx* alpha, cplx* bet
   const size_t smem = (size_t)3 * k * k * sizeof(cplx);
   const int use_smem = smem <= 200 * 1024;
   if (use_smem) {
-    cudaError_t e =
-        cudaFuncSetAttribute(qz_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = ie_smem_optin((const void*)qz_kernel);
     if (e != cudaSuccess) return e;
   }
   qz_kernel<<<1, 256, use_smem ? smem : 0, s>>>(k, Ah, Bh, Z, alpha, beta, M, VR, status,

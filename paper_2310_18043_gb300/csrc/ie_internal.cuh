@@ -66,6 +66,23 @@ __device__ __forceinline__ unsigned long long ie_globaltimer() {
   return t;
 }
 
+// Raises a kernel's dynamic shared-memory limit to the device's per-block opt-in maximum
+// (less its static shared memory). Every caller sets the same value, so launches of one kernel
+// from several host threads with different sizes cannot lower the limit under one another,
+// as setting the exact size before each launch would.
+inline cudaError_t ie_smem_optin(const void* kfn) {
+  int dev = 0, optin = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (e != cudaSuccess) return e;
+  cudaFuncAttributes fa;
+  e = cudaFuncGetAttributes(&fa, kfn);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              optin - (int)fa.sharedSizeBytes);
+}
+
 // Process-wide count of kernel launches issued by this library (exposed in ie_stats).
 void ie_count_launch();
 int64_t ie_launch_count();

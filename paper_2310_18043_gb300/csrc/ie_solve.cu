@@ -470,7 +470,7 @@ template <typename CT, int NC, int SPT, int REGS>
 static cudaError_t launch_solve_r(const SolveArgsT<CT>& a, int q, int threads, size_t smem,
                                   cudaStream_t s) {
   auto kfn = band_solve_kernel<CT, NC, SPT, REGS>;
-  cudaError_t e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = ie_smem_optin((const void*)kfn);
   if (e != cudaSuccess) return e;
   int blocks = 0;
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, kfn, threads, smem);

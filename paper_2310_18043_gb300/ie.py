@@ -57,10 +57,17 @@ class ie_stats(C.Structure):
         return {f: getattr(self, f) for f, _ in self._fields_}
 
 
+class ie_batch_item(C.Structure):
+    _fields_ = [("h", C.c_void_p), ("Y0_any", C.c_void_p), ("ldy0", C.c_int64),
+                ("h_lambda", C.c_void_p), ("X_any", C.c_void_p), ("ldx", C.c_int64),
+                ("h_rho", C.c_void_p), ("h_e", C.c_void_p), ("stream", C.c_void_p),
+                ("n_found", C.c_int32), ("status", C.c_int32), ("stats", ie_stats)]
+
+
 EXPORTS = ["ie_opts_default", "ie_create", "ie_destroy", "ie_status_str", "ie_filter_apply",
            "ie_apply_G", "ie_hsrr", "ie_solve", "ie_spmv", "ie_get_coeffs", "ie_get_factor",
            "ie_get_stats", "ie_apply_G_static", "ie_apply_GH", "ie_solve_left",
-           "ie_eig_sensitivity"]
+           "ie_eig_sensitivity", "ie_solve_batch"]
 
 _lib = None
 _vp, _i32, _i64, _dp = C.c_void_p, C.c_int32, C.c_int64, C.POINTER(C.c_double)
@@ -94,6 +101,7 @@ def load():
     L.ie_apply_GH.argtypes = [_vp, _vp, _i64, _i32, _vp, _i64, _vp]
     L.ie_solve_left.argtypes = [_vp, _vp, _i32, _vp, _i64, _vp, _i64, _vp, _vp,
                                 C.POINTER(ie_stats), _vp]
+    L.ie_solve_batch.argtypes = [C.POINTER(ie_batch_item), _i32, _i32]
     L.ie_eig_sensitivity.argtypes = [_vp, _vp, _i64, _vp, _i64, _i32, ie_complex, _vp, _i64, _vp,
                                      _vp, _vp]
     for f in EXPORTS:
@@ -276,6 +284,39 @@ def ie_eig_sensitivity(h, X, Y, alpha=1j, S=None, gbar=None, grad=None, stream=N
     return load().ie_eig_sensitivity(h, px, ldx, py, ldy, nf, ie_complex(a.real, a.imag), ps,
                                      lds if S is not None else 0, _vec(gb), _vec(grad),
                                      _stream(stream))
+
+
+def ie_solve_batch(problems, max_workers=0, streams=None):
+    """problems: list of (handle, Y0 or None, X, k). Runs their drivers concurrently
+    (ie_solve_batch). Returns (status, [dict(status, lam, rho, e, n_found, stats)])."""
+    nb = len(problems)
+    items = (ie_batch_item * nb)()
+    keep = []
+    for i, (h, Y0, X, k) in enumerate(problems):
+        p0, ld0, _, _ = _block(Y0)
+        px, ldx, _, _ = _block(X)
+        lam = np.zeros(k, dtype=np.complex128)
+        rho = np.zeros(k)
+        e = np.zeros(k)
+        keep.append((lam, rho, e))
+        it = items[i]
+        it.h = h.value if isinstance(h, C.c_void_p) else h
+        it.Y0_any = p0.value if p0 is not None else None
+        it.ldy0 = ld0 if Y0 is not None else 0
+        it.h_lambda = lam.ctypes.data
+        it.X_any = px.value
+        it.ldx = ldx
+        it.h_rho = rho.ctypes.data
+        it.h_e = e.ctypes.data
+        s_ = streams[i] if streams is not None else None
+        it.stream = (s_ if isinstance(s_, int) else s_.cuda_stream) if s_ is not None else None
+    st = load().ie_solve_batch(items, nb, int(max_workers))
+    out = []
+    for i in range(nb):
+        lam, rho, e = keep[i]
+        out.append({"status": items[i].status, "lam": lam, "rho": rho, "e": e,
+                    "n_found": items[i].n_found, "stats": items[i].stats.as_dict()})
+    return st, out
 
 
 def ie_get_coeffs(h, p, q):

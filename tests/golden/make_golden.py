@@ -10,6 +10,11 @@ computed exactly: the centre is the eigenvalue nearest the point
 (4/h^2)/1.025 + i*mean(gamma) -- the median of the unperturbed operator scaled by
 the mean of B's diagonal (checked against the exact median at small m by this script).
 
+Batch workloads (ie_inputs.batch_problems): the proxy point is the closed-form eigenvalue
+of the constant-coefficient operator at the fraction proxy_frac of its sorted spectrum,
+scaled by 1/1.025, plus i*mean(gamma); then the same nearest-eigenvalue centre and
+N-eigenvalue radius.
+
 Usage: python tests/golden/make_golden.py [names...]
 """
 import json
@@ -41,11 +46,17 @@ SPECS = {
     # precision: m=512 (n=262,144, band 512), q=p=8, k=96, mixed-precision solves
     "c4_m512": dict(m=512, seed=0, p=8, q=8, k=96, n_in=60, driver=2, precision=1),
 }
+# the batched-solver mix (12 problems: grids 64..192, 1-2 disks each)
+for _b in ie_inputs.batch_problems(12, 0):
+    SPECS[_b["name"]] = {k_: v for k_, v in _b.items() if k_ != "name"}
 
 
-def proxy_center(pen):
-    h = 1.0 / (pen.m + 1)
-    return (4.0 / h**2) / 1.025 + 1j * float(np.mean(pen.gamma))
+def proxy_center(pen, frac=None):
+    if frac is None:
+        h = 1.0 / (pen.m + 1)
+        return (4.0 / h**2) / 1.025 + 1j * float(np.mean(pen.gamma))
+    lam = ie_inputs.closed_form_spectrum(pen.m)
+    return lam[int(frac * pen.n)] / 1.025 + 1j * float(np.mean(pen.gamma))
 
 
 def build(name, spec):
@@ -63,7 +74,7 @@ def build(name, spec):
         info["median_exact"] = True
         info["proxy_center_offset"] = abs(proxy_center(pen) - c)
     else:
-        c0 = proxy_center(pen)
+        c0 = proxy_center(pen, spec.get("proxy_frac"))
         near0 = ref.nearest_eigenvalues(A, B, c0, 8)
         c = near0[0]
         # Shift-invert from two shifts that are not eigenvalues (c itself is one): the

@@ -62,6 +62,36 @@ def test_struct_layouts_match_header():
     assert [f for f, _ in ie.ie_opts._fields_] == fields("ie_opts")
     assert [f for f, _ in ie.ie_stats._fields_] == fields("ie_stats")
     assert [f for f, _ in ie.ie_pencil._fields_] == fields("ie_pencil")
+    assert [f for f, _ in ie.ie_batch_item._fields_] == fields("ie_batch_item")
+
+
+def test_struct_offsets_match_c_compiler(tmp_path):
+    """sizeof and every field offset of the ABI structs, as gcc lays them out from the
+    header, equal the binding's ctypes layout."""
+    import shutil
+    import subprocess
+    import paper_2310_18043_gb300.ie as ie
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    structs = {"ie_opts": ie.ie_opts, "ie_stats": ie.ie_stats, "ie_pencil": ie.ie_pencil,
+               "ie_batch_item": ie.ie_batch_item, "ie_complex": ie.ie_complex}
+    lines = ["#include <stdio.h>", "#include <stddef.h>", f'#include "{HEADER}"', "int main(void) {"]
+    for name, cls in structs.items():
+        lines.append(f'  printf("{name} %zu\\n", sizeof({name}));')
+        for f, _ in cls._fields_:
+            lines.append(f'  printf("{name}.{f} %zu\\n", offsetof({name}, {f}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-std=c99", "-o", str(exe), str(src)], check=True)
+    got = dict(l.rsplit(" ", 1) for l in subprocess.run([str(exe)], check=True,
+               capture_output=True, text=True).stdout.splitlines())
+    for name, cls in structs.items():
+        assert int(got[name]) == ctypes.sizeof(cls), name
+        for f, _ in cls._fields_:
+            assert int(got[f"{name}.{f}"]) == getattr(cls, f).offset, (name, f)
 
 
 def test_status_strings_and_defaults(lib):
