@@ -49,6 +49,9 @@ def parse():
     ap.add_argument("--mixed", type=int, default=1,
                     help="1 (with --precision 0): also report the mixed-precision path on the same "
                          "workload (throughput and time to all eigenpairs at the same residual)")
+    ap.add_argument("--simple", type=int, default=1,
+                    help="1: also time the p*q-pole simple rule (p = 1) on the same workload, "
+                         "the paper's comparison of Sec. 6 (Tables 3-4)")
     ap.add_argument("--batch", type=int, default=1,
                     help="1: also time the batched solver on the seeded 12-problem mix "
                          "(sequential ie_solve vs ie_solve_batch)")
@@ -309,6 +312,10 @@ def run_native(args):
                                     "peak_tflops": FP32_PEAK_TFLOPS},
                  "time_to_all_eigenpairs": time_solves(1) if args.solve else None}
 
+    simple = None
+    if args.simple and rank == 0:
+        simple = time_simple_rule(ie, w, pen, A_d, B_d, device, stream, Xd, args.precision)
+
     batch = None
     if args.batch and rank == 0:
         batch = time_batch(ie, device, stream)
@@ -362,6 +369,7 @@ def run_native(args):
             "mixed_precision": mixed,
             "sensitivities": sens,
             "batch": batch,
+            "simple_rule": simple,
             "e2e": e2e,
             "clocks": clk.summary(),
             "cpu_baseline": cpu,
@@ -369,6 +377,45 @@ def run_native(args):
         print(json.dumps(line))
     if dist is not None:
         dist.destroy_process_group()
+
+
+def time_simple_rule(ie, w, pen, A_d, B_d, device, stream, Xd, precision):
+    """The paper's comparison (Sec. 6, Tables 3-4): the simple trapezoidal rule with the same
+    number of poles N = p*q (a handle with p = 1, q = N: N factorisations, no GMRES) against
+    the composite rule (q factorisations + multi-shift GMRES, in time_to_all_eigenpairs),
+    time to all eigenpairs by Alg. 1 at the same 1e-10 residual."""
+    import torch
+
+    import ie_inputs
+    n, k = pen.n, w["k"]
+    N = w["p"] * w["q"]
+    o = ie.ie_opts_default(k=k, m_max=150, precision=precision, driver=1)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    st, h = ie.ie_create(n, pen.offsets, A_d, B_d, w["center"], w["radius"], 1, N, o, stream)
+    torch.cuda.synchronize()
+    t_create = time.perf_counter() - t0
+    if st != ie.IE_OK:
+        return {"error": ie.ie_status_str(st)}
+    Y0 = ie_inputs.orthonormal_random_block(n, k, seed=w["seed"])
+    Y0d = torch.from_numpy(np.ascontiguousarray(Y0.T)).to(device).T
+    t0 = time.perf_counter()
+    st1, lam, rho, e, nf, sst = ie.ie_solve(h, Y0d, Xd, k, stream)
+    torch.cuda.synchronize()
+    t_solve = time.perf_counter() - t0
+    ref = np.array(w["eig_in_disk_re"]) + 1j * np.array(w["eig_in_disk_im"])
+    got = lam[:nf]
+    err = (float(np.max(np.min(np.abs(got[:, None] - ref[None, :]), axis=1) / np.abs(got)))
+           if nf else None)
+    ie.ie_destroy(h)
+    kl = pen.half_bw
+    return {"poles": N, "p": 1, "factor_bytes": N * n * (3 * kl + 1) * 16,
+            "create_s": t_create, "factor_ms": sst["t_factor_ms"], "solve_s": t_solve,
+            "seconds": t_create + t_solve, "status": ie.ie_status_str(st1), "n_found": nf,
+            "n_in_disk_reference": int(len(ref)),
+            "max_rho": float(np.max(rho[:nf])) if nf else None,
+            "max_rel_err_vs_reference": err, "outer_iters": sst["outer_iters"],
+            "filter_ms": sst["t_filter_ms"], "hsrr_ms": sst["t_hsrr_ms"]}
 
 
 def time_batch(ie, device, stream, workers=12):

@@ -168,3 +168,36 @@ def test_sensitivity_kernel_matches_oracle_formula_host_buffers(ie):
         assert ie.ie_eig_sensitivity(c.h, X, Y, 1j, None, None, gh) == ie.IE_ERR_ARG
     finally:
         c.close()
+
+
+def test_autograd_function_gradient_matches_oracle(ie):
+    """DiskEigenvalues (torch.autograd.Function over the C ABI): the eigenvalues in D of the
+    C1 pencil as a function of gamma, and d/dgamma of L = sum_i w_i Re(lambda_i) + Im(lambda_0)
+    by loss.backward(), against the oracle's VJP on LAPACK's left and right eigenvectors."""
+    from paper_2310_18043_gb300.autograd import DiskEigenvalues
+    w = ie_inputs.load_workload("c1_m24")
+    pen = ie_inputs.make_pencil(w["m"], w["seed"])
+    main = int(np.flatnonzero(pen.offsets == 0)[0])
+    A0 = pen.A_dia.copy()
+    A0[main] -= 1j * pen.gamma
+    dev = "cuda:0"
+    gamma = torch.tensor(pen.gamma, dtype=torch.float64, device=dev, requires_grad=True)
+    opts = ie.ie_opts_default(k=w["k"], driver=1)
+    lam = DiskEigenvalues.apply(gamma, torch.from_numpy(A0).to(dev),
+                                torch.from_numpy(pen.B_dia).to(dev), pen.offsets, w["center"],
+                                w["radius"], w["p"], w["q"], opts)
+    nf = lam.shape[0]
+    assert nf == len(w["eig_in_disk_re"])
+    wts = torch.from_numpy(np.random.default_rng(4).uniform(0, 1, nf)).to(dev)
+    loss = (wts * lam.real).sum() + lam[0].imag
+    loss.backward()
+    A, B = opencil.pencil_matrices(pen)
+    lam_d, VL, VR = sla.eig(A.toarray(), B.toarray(), left=True, right=True)
+    lam_h = lam.detach().cpu().numpy()
+    sel = [int(np.argmin(np.abs(lam_d - l))) for l in lam_h]
+    Sref = oadj.diag_sensitivity(B, VR[:, sel], VL[:, sel], alpha=1j)
+    gbar = wts.cpu().numpy().astype(np.complex128)
+    gbar[0] += 1j
+    gref = oadj.vjp(Sref, gbar)
+    got = gamma.grad.cpu().numpy()
+    assert np.linalg.norm(got - gref) <= 1e-8 * np.linalg.norm(gref)

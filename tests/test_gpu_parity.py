@@ -331,3 +331,33 @@ def test_singular_pencil_reports_zero_pivot(ie):
                          10.0, 2.5, 4, 4, ie.ie_opts_default(k=4))
     assert st == ie.IE_ERR_SINGULAR
     ie.ie_destroy(h)
+
+
+# ---------------------------------------------------------------- simple rule (p = 1)
+def test_simple_rule_handle_equals_composite(ie, c1):
+    """p = 1 leaves no outer shift (the root -1 of z = -1 is dropped, Thm 2), so the filter is
+    the q-point simple rule U = G(Y) with no GMRES. A handle with p = 1, q = p*q of the
+    composite handle applies the same R_{c,r,pq}(B^{-1}A) (Thm 2), and its driver finds the
+    same eigenvalues."""
+    w = c1.w
+    s = Case(ie, "c1_m24", p=1, q=w["p"] * w["q"])
+    try:
+        k = w["k"]
+        Y = ie_inputs.orthonormal_random_block(c1.n, k, seed=2)
+        Uc, Us = dzeros(c1.n, k), dzeros(c1.n, k)
+        assert ie.ie_filter_apply(c1.h, dblock(Y), Uc) == ie.IE_OK
+        assert ie.ie_filter_apply(s.h, dblock(Y), Us) == ie.IE_OK
+        _, st = ie.ie_get_stats(s.h)
+        assert st["gmres_iters_max"] == 0
+        a, b = Uc.cpu().numpy(), Us.cpu().numpy()
+        assert np.linalg.norm(a - b) / np.linalg.norm(a) < 1e-9
+        Xd = dzeros(c1.n, k)
+        Y0 = ie_inputs.orthonormal_random_block(c1.n, k, seed=w["seed"])
+        st, lam, rho, e, nf, _ = ie.ie_solve(s.h, dblock(Y0), Xd, k)
+        assert st == ie.IE_OK
+        ref = golden_eigs(w)
+        assert nf == len(ref)
+        match_eigs(lam[:nf], ref)
+        assert np.all(rho[:nf] <= 1e-10)
+    finally:
+        s.close()
