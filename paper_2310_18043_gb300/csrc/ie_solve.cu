@@ -14,6 +14,7 @@
 // Factor columns (L parts forward, U parts backward, with pivots / 1/u_jj) are staged NB at a
 // time into a shared ring by cp.async.bulk (TMA bulk copies) with mbarrier completion; every
 // wait is bounded.
+#include <cstdio>
 #include <cstdlib>
 #include <map>
 #include <mutex>
@@ -564,6 +565,14 @@ bool tune_enabled() {
   }();
   return on;
 }
+// IE_SOLVE_TUNE_LOG=1: print each tuning decision (candidate shapes and times) to stderr
+bool tune_log() {
+  static const bool on = [] {
+    const char* e = getenv("IE_SOLVE_TUNE_LOG");
+    return e && e[0] == '1';
+  }();
+  return on;
+}
 }  // namespace
 
 template <typename CT>
@@ -619,6 +628,14 @@ static cudaError_t launch_tuned(const SolveArgsT<CT>& a, int q, cudaStream_t s) 
           if (T.ms[i] < T.ms[b]) b = i;
         T.best = b;
         use = T.cand[b];
+        if (tune_log()) {
+          fprintf(stderr, "band solve tuner (elem %d B, kl %d, q %d, k <= %d):", key.esize, key.kl,
+                  key.q, key.kb);
+          for (size_t i = 0; i < T.cand.size(); ++i)
+            fprintf(stderr, " [nc %d spt %d stages %d: %.3f ms]", T.cand[i].nc, T.cand[i].spt,
+                    T.cand[i].stages, T.ms[i]);
+          fprintf(stderr, " -> %d\n", b);
+        }
       } else if (T.next < (int)T.cand.size()) {
         slot = T.next++;
         use = T.cand[slot];
