@@ -32,6 +32,12 @@ sys.path.insert(0, ROOT)
 WORKLOAD = "c2_m256"
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12     # 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # 152 SMs x 128 FP32 FMA/clk x 2 flop x 2.07 GHz
+# DRAM traffic of one complex128 band_solve_kernel launch per algorithmic byte, from the ncu
+# capture at p1_m160 (profiles/band_solve_blocked_c128_p1_m160.md): dram__bytes_read.sum +
+# dram__bytes_write.sum = 1.938303e9 + 0.399454e9 B against 2.231832e9 algorithmic bytes. The
+# traffic is the factors (q n (kl + kv) entries, once) plus the blocks, so it scales with the
+# algorithmic bytes; the bench workload's traffic is this ratio times its algorithmic bytes.
+C128_SOLVE_TRAFFIC_RATIO = (1.938303e9 + 0.399454e9) / 2.231832e9
 
 
 def parse():
@@ -359,7 +365,10 @@ def run_native(args):
                                         if args.precision == 0 else
                                         ("derived: 152 SMs x 128 FP32 FMA/clk x 2 flop x 2.07 GHz "
                                          "(measured FP32 FMA probe: 70.2 TFLOP/s)"),
-                         "traffic": None,
+                         "traffic": (C128_SOLVE_TRAFFIC_RATIO * solve_by / launches
+                                     if (args.precision == 0 and launches and solve_by) else None),
+                         "traffic_source": ("ncu capture at p1_m160 scaled by algorithmic bytes"
+                                            if args.precision == 0 else None),
                          "algorithmic_bytes_per_launch": solve_by / launches if (launches and solve_by) else None,
                          "algorithmic_flops_per_launch": solve_fl / launches if launches else None,
                          "launches": launches, "avg_launch_ms": solve_ms / launches if launches else None,
