@@ -432,7 +432,8 @@ def time_batch(ie, device, stream, workers=12):
     q 4..8, p 4..8; tests/golden/workloads.json b*), complex128, Alg. 1: every problem solved
     alone with ie_solve one after another, against all of them through ie_solve_batch
     (one host worker and one stream per problem). Factorisations are done before and reported
-    apart. One untimed batch run first lets the launch-shape tuner settle for both timings."""
+    apart. One untimed pass, one problem at a time, lets the launch-shape tuner settle (timing
+    its candidates without other problems running) before both timings."""
     import torch
 
     import ie_inputs
@@ -461,7 +462,8 @@ def time_batch(ie, device, stream, workers=12):
         X = torch.zeros((w["k"], pen.n), dtype=torch.complex128, device=device).T
         refs.append(np.array(w["eig_in_disk_re"]) + 1j * np.array(w["eig_in_disk_im"]))
         probs.append((h, Y0d, X, w["k"]))
-    ie.ie_solve_batch(probs, max_workers=workers)          # warm-up (tuner)
+    for (h, Y0d, X, k) in probs:      # warm-up, one at a time: the tuner times shapes alone
+        ie.ie_solve(h, Y0d, X, k, stream)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     seq = []

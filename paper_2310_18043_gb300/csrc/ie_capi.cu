@@ -102,6 +102,7 @@ struct ie_handle_s {
   int lu_ctas = 0;
   // mixed precision (opts.precision = 1): complex64 factors and FP32-solve scratch
   int precision = 0, refine = 2, klp = 0;
+  int refine_cur = -1;     // refinement steps for the next G-application (-1: refine)
   float2* L32 = nullptr;   // q * n_pad * klp
   float2* U32 = nullptr;   // q * n_pad * kv
   float2* dinv32 = nullptr;
@@ -633,7 +634,8 @@ static ie_status apply_G_mixed(ie_handle h, int k, cplx* GV, int64_t ldg, cudaSt
   const double flops = q * k * (8.0 * (fwd + bwd) + 12.0 * nn);
   const bool adj = h->side != 0;
   launch_to_c64(n, k, h->BVw, n, h->BV32, n, s);
-  for (int it = 0; it <= h->refine; ++it) {
+  const int nref = h->refine_cur >= 0 ? std::min(h->refine_cur, h->refine) : h->refine;
+  for (int it = 0; it <= nref; ++it) {
     if (it > 0)
       launch_pole_residual(h->pen(), adj ? h->d_pconj : h->d_poles, h->q, k, h->BVw, n, h->Xp, n,
                            ps, h->R32, n, ps, s);
@@ -662,6 +664,21 @@ static ie_status apply_G_mixed(ie_handle h, int k, cplx* GV, int64_t ldg, cudaSt
   launch_pole_wsum(h->q, n, k, h->Xp, n, ps, adj ? h->d_wconj : h->d_weights, GV, ldg, s);
   h->g_columns += k;
   return IE_OK;
+}
+
+// Refinement steps for an Arnoldi step of the mixed-precision path, relaxed as GMRES converges
+// (inexact Krylov methods: Bouras & Fraysse, SIAM J. Matrix Anal. Appl. 26, 2005; Simoncini &
+// Szyld, SIAM J. Sci. Comput. 25, 2003): an operator error eps at a step whose residual is r
+// changes the final residual by about eps * r, so eps may grow as r falls. With s refinement
+// steps the relative error of K_i^{-1} b is taken as 1e-3, 1e-8, 1e-13 for s = 0, 1, 2 (ten
+// times the errors measured for complex64 factors), and the fewest steps with
+// eps_s * r <= tol / 50 are used (50: a bound on the number of steps that add such errors).
+static int relaxed_refine(const ie_handle h, double r) {
+  static const double eps[3] = {1e-3, 1e-8, 1e-13};
+  const double tol = h->opts.gmres_tol;
+  for (int s_ = 0; s_ < h->refine && s_ < 3; ++s_)
+    if (eps[s_] * r <= tol / 50.0) return s_;
+  return h->refine;
 }
 
 // ------------------------------ filter (multi-shift GMRES) -----------------------------------
@@ -695,6 +712,7 @@ static ie_status filter_dev(ie_handle h, const cplx* Y, int64_t ldy, int k, cplx
   const double tol = h->opts.gmres_tol;
   std::vector<int> act;
   std::vector<double> res(k);
+  double rmax = 1.0;   // largest relative GMRES residual among the active columns so far
   // convergence state of every column for the current shift set
   for (int c = 0; c < k; ++c) h->conv_h[c] = (h->beta_h[c] > 0.0) ? 0 : 1;
   if (nshift == 0) {
@@ -709,8 +727,12 @@ static ie_status filter_dev(ie_handle h, const cplx* Y, int64_t ldy, int k, cplx
                     h->gvec, 1, h->d_res, s);
       CK(cudaMemcpyAsync(res.data(), h->d_res, sizeof(double) * act.size(), cudaMemcpyDeviceToHost, s));
       CK(cudaStreamSynchronize(s));
-      for (size_t i = 0; i < act.size(); ++i)
+      rmax = 0.0;
+      for (size_t i = 0; i < act.size(); ++i) {
         if (res[i] <= tol) h->conv_h[act[i]] = 1;
+        else rmax = std::max(rmax, res[i]);
+      }
+      if (rmax == 0.0) rmax = 1.0;
     }
   }
   while (true) {
@@ -724,17 +746,22 @@ static ie_status filter_dev(ie_handle h, const cplx* Y, int64_t ldy, int k, cplx
     const int kact = (int)act.size();
     CK(cudaMemcpyAsync(h->d_act, act.data(), sizeof(int) * kact, cudaMemcpyHostToDevice, s));
     launch_active_offsets(h->K, h->d_act, kact, h->d_off, s);
-    CKS(apply_G_dev(h, h->K.V, n, h->d_off, kact, h->Wb, n, s));   // w = G v_j
+    if (h->precision == 1) h->refine_cur = relaxed_refine(h, rmax);
+    const ie_status ga = apply_G_dev(h, h->K.V, n, h->d_off, kact, h->Wb, n, s);   // w = G v_j
+    h->refine_cur = -1;
+    CKS(ga);
     launch_arnoldi_cgs2(h->K, h->d_act, kact, h->Wb, n, h->hbuf, h->scratch, s);
     launch_givens(h->K, h->d_act, kact, h->d_shifts, nshift, h->rot_c, h->rot_s, h->gvec, 0,
                   h->d_res, s);
     CK(cudaMemcpyAsync(res.data(), h->d_res, sizeof(double) * kact, cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     flush_solve_timing(h);
+    rmax = 0.0;
     for (int i = 0; i < kact; ++i) {
       const int c = act[i];
       h->jc_h[c] += 1;
       if (res[i] <= tol) h->conv_h[c] = 1;
+      else rmax = std::max(rmax, res[i]);
     }
   }
   launch_krylov_combine(h->K, k, h->d_shifts, h->d_cw, nshift, odd, h->Rscr, h->zbuf, U, ldu, s);
