@@ -325,6 +325,8 @@ def run_native(args):
     batch = None
     if args.batch and rank == 0:
         batch = time_batch(ie, device, stream)
+        if args.mixed:
+            batch["mixed_precision"] = time_batch(ie, device, stream, precision=1)
 
     sens = None
     if args.sens and rank == 0:
@@ -427,9 +429,10 @@ def time_simple_rule(ie, w, pen, A_d, B_d, device, stream, Xd, precision):
             "filter_ms": sst["t_filter_ms"], "hsrr_ms": sst["t_hsrr_ms"]}
 
 
-def time_batch(ie, device, stream, workers=12):
+def time_batch(ie, device, stream, workers=12, precision=0):
     """The seeded mix of 12 independent problems (grids 64..192, 1-2 disks per pencil, k 16..32,
-    q 4..8, p 4..8; tests/golden/workloads.json b*), complex128, Alg. 1: every problem solved
+    q 4..8, p 4..8; tests/golden/workloads.json b*), Alg. 1, complex128 (precision 0) or
+    complex64 solves with FP64 refinement (precision 1): every problem solved
     alone with ie_solve one after another, against all of them through ie_solve_batch
     (one host worker and one stream per problem). Factorisations are done before and reported
     apart. One untimed pass, one problem at a time, lets the launch-shape tuner settle (timing
@@ -445,7 +448,7 @@ def time_batch(ie, device, stream, workers=12):
         pen = ie_inputs.make_pencil(w["m"], w["seed"])
         A_d = torch.from_numpy(pen.A_dia).to(device)
         B_d = torch.from_numpy(pen.B_dia).to(device)
-        o = ie.ie_opts_default(k=w["k"], m_max=150, driver=w["driver"])
+        o = ie.ie_opts_default(k=w["k"], m_max=150, driver=w["driver"], precision=precision)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         st, h = ie.ie_create(pen.n, pen.offsets, A_d, B_d, w["center"], w["radius"], w["p"],
@@ -485,7 +488,10 @@ def time_batch(ie, device, stream, workers=12):
             errs.append(float(np.max(np.min(np.abs(got[:, None] - ref[None, :]), axis=1) / np.abs(got))))
     for h in hs:
         ie.ie_destroy(h)
-    return {"problems": len(names), "workers": workers, "create_s_total": t_create,
+    return {"problems": len(names), "workers": workers, "precision": precision,
+            "max_rho": max((float(np.max(r["rho"][: r["n_found"]])) for r in res if r["n_found"]),
+                           default=None),
+            "create_s_total": t_create,
             "sequential_s": t_seq, "batched_s": t_bat,
             "problems_per_s_sequential": len(names) / t_seq,
             "problems_per_s_batched": len(names) / t_bat, "speedup": t_seq / t_bat,
