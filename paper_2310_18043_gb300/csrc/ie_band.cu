@@ -106,10 +106,15 @@ void launch_norm1_cols(const DiaDev& P, int which, double* d_out, double* /*scra
 // for each column j: pivot row j+tp = argmax_t |re|+|im| of column j rows j..j+kl (first max);
 // ju = max(ju, min(j + ku + tp, n-1)); swap rows j and j+tp in columns j..ju; multipliers
 // l_t = a(j+t, j) / pivot; rank-1 update of rows j+1..j+kl in columns j+1..ju.
-// Grid = q poles x P CTAs; CTA b owns the columns l with l % P == b. All CTAs of a pole read
-// the pivot column and compute the pivot and multipliers redundantly; the owner of column j
-// writes its final entries (U(j,j), L, piv, 1/pivot) after the step's barrier, when no CTA
-// reads column j any more. One bounded per-pole barrier per column.
+// Grid = q poles x P CTAs; CTA b owns the columns l with l % P == b, and only it reads or
+// writes them. Look-ahead: at step j the owner of column j+1 applies step j to that column
+// first, finds its pivot and multipliers, writes its final entries (U(j+1,j+1), L, piv,
+// 1/pivot) and publishes (pivot offset, multipliers) for step j+1 in a per-pole ring slot,
+// then sets the slot's flag with release semantics. Every other CTA of the pole waits only on
+// that flag (bounded, abort-aware) before applying step j+1 to its own columns, so no barrier
+// spans the pole and the owner's next pivot overlaps the other CTAs' updates. A CTA can run
+// at most P steps ahead of another (each CTA owns one column in any P consecutive ones, and
+// its pivot gates that step), so R >= P + 2 ring slots are never overwritten while read.
 
 __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
   unsigned v;
@@ -120,22 +125,19 @@ __device__ __forceinline__ int ld_volatile_i32(const int* p) {
   return *(const volatile int*)p;
 }
 
-__device__ bool pole_barrier(unsigned* cnt, unsigned* gen, unsigned nb, unsigned& my_gen,
-                             int* status) {
+__device__ __forceinline__ void st_release_u32(unsigned* p, unsigned v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Waits (thread 0 of the CTA) until flag == want; false on timeout or abort.
+__device__ bool lu_wait_flag(const unsigned* flag, unsigned want, int* status) {
   __shared__ int s_ok;
-  __syncthreads();
   if (threadIdx.x == 0) {
     int ok = 1;
-    const unsigned g = my_gen;
-    __threadfence();
-    if (atomicAdd(cnt, 1u) == nb - 1) {
-      atomicExch(cnt, 0u);
-      __threadfence();
-      atomicAdd(gen, 1u);
-    } else {
+    if (ld_acquire_u32(flag) != want) {
       const unsigned long long t0 = ie_globaltimer();
       unsigned it = 0;
-      while (ld_acquire_u32(gen) == g) {
+      while (ld_acquire_u32(flag) != want) {
         if ((++it & 15u) == 0) {
           if (ld_volatile_i32(status + ST_ABORT)) { ok = 0; break; }
           if (ie_globaltimer() - t0 > IE_WAIT_NS) {
@@ -147,8 +149,6 @@ __device__ bool pole_barrier(unsigned* cnt, unsigned* gen, unsigned nb, unsigned
         }
       }
     }
-    __threadfence();
-    my_gen = g + 1;
     s_ok = ok;
   }
   __syncthreads();
@@ -157,53 +157,42 @@ __device__ bool pole_barrier(unsigned* cnt, unsigned* gen, unsigned nb, unsigned
 
 __global__ void __launch_bounds__(512) band_lu_kernel(int64_t n, int kl, int ldab, int64_t n_pad,
                                                       cplx* AB, int* piv, cplx* dinv,
-                                                      unsigned* bar, int* status, int P,
-                                                      int nown_max) {
+                                                      cplx* ring, int* ring_tp,
+                                                      unsigned* ring_flag, int R, int* status,
+                                                      int P, int nown_max) {
   const int pole = blockIdx.x / P, b = blockIdx.x % P;
   const int T = blockDim.x, tid = threadIdx.x;
   const int kv = 2 * kl;
   cplx* A = AB + (int64_t)pole * n_pad * ldab;
   int* pv_out = piv + (int64_t)pole * n_pad;
   cplx* di_out = dinv + (int64_t)pole * n_pad;
+  cplx* rmul = ring + (int64_t)pole * R * (kl + 1);
+  int* rtp = ring_tp + (int64_t)pole * R;
+  unsigned* rflag = ring_flag + (int64_t)pole * R;
   extern __shared__ double2 lu_sm[];
-  cplx* col = lu_sm;                 // kl+1
-  cplx* mult = col + (kl + 1);       // kl+1
-  cplx* urow = mult + (kl + 1);      // nown_max
+  cplx* mult = lu_sm;                // kl+1: multipliers of the current step
+  cplx* col = mult + (kl + 1);       // kl+1: pivot column of the next step (owner)
+  cplx* urow = col + (kl + 1);       // nown_max
   cplx* arow = urow + nown_max;      // nown_max
   __shared__ double red_v[32];
   __shared__ int red_i[32];
   __shared__ int s_tp;
-  unsigned* cnt = bar + 2 * pole;
-  unsigned* gen = bar + 2 * pole + 1;
-  unsigned my_gen = 0;
-  int64_t ju = 0;
-  int prev_tp = 0, prev_nrows = -1;
-  cplx prev_pv = cmk(0, 0), prev_rcp = cmk(0, 0);
+  __shared__ cplx s_u, s_a;
 
-  for (int64_t j = 0; j < n; ++j) {
-    // (a) final entries of column j-1, written by its owner once nobody reads it
-    if (j > 0 && ((j - 1) % P) == b) {
-      cplx* cj = A + (j - 1) * ldab + kv;
-      for (int t = tid; t <= prev_nrows; t += T) cj[t] = (t == 0) ? prev_pv : mult[t];
-      if (tid == 0) {
-        pv_out[j - 1] = (int)(j - 1 + prev_tp);
-        di_out[j - 1] = prev_rcp;
-      }
-    }
-    __syncthreads();
-    // (b) pivot column rows j..j+nrows
-    const int nrows = (int)((n - 1 - j) < (int64_t)kl ? (n - 1 - j) : (int64_t)kl);
-    const cplx* cj = A + j * ldab + kv;
+  // pivot search, multipliers, final column entries and publication of step jc (owner of
+  // column jc only); column jc holds all updates of steps < jc in global memory
+  auto pivot_publish = [&](int64_t jc) {
+    const int nr = (int)((n - 1 - jc) < (int64_t)kl ? (n - 1 - jc) : (int64_t)kl);
+    cplx* cj = A + jc * ldab + kv;
     double best = -1.0;
     int bi = 0;
-    for (int t = tid; t <= nrows; t += T) {
+    for (int t = tid; t <= nr; t += T) {
       const cplx v = __ldcg(cj + t);
       col[t] = v;
       const double a = cabs1(v);
       if (a > best) { best = a; bi = t; }
     }
-    // (c) argmax, first index on ties
-    for (int o = 16; o > 0; o >>= 1) {
+    for (int o = 16; o > 0; o >>= 1) {   // argmax, first index on ties
       const double ob = __shfl_xor_sync(0xffffffffu, best, o);
       const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
       if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
@@ -220,16 +209,62 @@ __global__ void __launch_bounds__(512) band_lu_kernel(int64_t n, int kl, int lda
     __syncthreads();
     const int tp = s_tp;
     const cplx pv = col[tp];
-    { const int64_t cand = (j + kl + tp < n - 1) ? (j + kl + tp) : (n - 1); if (cand > ju) ju = cand; }
     const bool zero = (pv.x == 0.0 && pv.y == 0.0);
-    if (zero && b == 0 && tid == 0) atomicMax(status + ST_SINGULAR, 1);
     const cplx rcp = zero ? cmk(0, 0) : crcp(pv);
-    for (int t = 1 + tid; t <= nrows; t += T)
-      mult[t] = zero ? cmk(0, 0) : cmul((t == tp) ? col[0] : col[t], rcp);
-    // (d) swap + rank-1 update of the owned columns l in (j, ju], l % P == b
-    const int64_t jn = j + 1;
+    cplx* slot = rmul + (int64_t)(jc % R) * (kl + 1);
+    for (int t = tid; t <= nr; t += T) {
+      if (t == 0) {
+        cj[0] = pv;
+      } else {
+        const cplx m = zero ? cmk(0, 0) : cmul((t == tp) ? col[0] : col[t], rcp);
+        cj[t] = m;
+        slot[t] = m;
+      }
+    }
+    if (tid == 0) {
+      if (zero) atomicMax(status + ST_SINGULAR, 1);
+      pv_out[jc] = (int)(jc + tp);
+      di_out[jc] = rcp;
+      rtp[jc % R] = tp;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      __threadfence();
+      st_release_u32(rflag + (jc % R), (unsigned)(jc + 1));
+    }
+  };
+
+  if (n > 0 && b == 0) pivot_publish(0);
+  int64_t ju = 0;
+  for (int64_t j = 0; j < n; ++j) {
+    // (a) step j's pivot offset and multipliers, published by the owner of column j
+    if (!lu_wait_flag(rflag + (j % R), (unsigned)(j + 1), status)) return;
+    const int nrows = (int)((n - 1 - j) < (int64_t)kl ? (n - 1 - j) : (int64_t)kl);
+    const cplx* slot = rmul + (int64_t)(j % R) * (kl + 1);
+    for (int t = 1 + tid; t <= nrows; t += T) mult[t] = __ldcg(slot + t);
+    const int tp = __ldcg(rtp + (j % R));
+    { const int64_t cand = (j + kl + tp < n - 1) ? (j + kl + tp) : (n - 1); if (cand > ju) ju = cand; }
+    __syncthreads();
+    // (b) look-ahead: the owner of column j+1 applies step j to it, then publishes step j+1
+    const bool own_next = (j + 1 < n) && ((j + 1) % P == b);
+    if (own_next) {
+      if (j + 1 <= ju && nrows > 0) {
+        cplx* cl = A + (j + 1) * ldab + kv - 1;      // row j of column j+1
+        if (tid == 0) { s_u = __ldcg(cl + tp); s_a = __ldcg(cl); }
+        __syncthreads();
+        const cplx u = s_u, a0 = s_a;
+        for (int t = tid; t <= nrows; t += T) {
+          if (t == 0) cl[0] = u;
+          else cl[t] = cfms(mult[t], u, (t == tp) ? a0 : __ldcg(cl + t));
+        }
+        __syncthreads();
+      }
+      pivot_publish(j + 1);
+    }
+    // (c) swap + rank-1 update of the other owned columns l in (j, ju], l % P == b
+    const int64_t jn = own_next ? j + 2 : j + 1;    // column j+1 is done when owned here
     const int64_t l0 = jn + (((int64_t)b - jn % P) % P + P) % P;
-    const int nown = (!zero && l0 <= ju) ? (int)((ju - l0) / P + 1) : 0;
+    const int nown = (l0 <= ju && nrows >= 0) ? (int)((ju - l0) / P + 1) : 0;
     for (int idx = tid; idx < nown; idx += T) {
       const int64_t l = l0 + (int64_t)idx * P;
       const cplx* cl = A + l * ldab + kv - (l - j);   // row j of column l
@@ -268,25 +303,21 @@ __global__ void __launch_bounds__(512) band_lu_kernel(int64_t n, int kl, int lda
       const int64_t l = l0 + (int64_t)idx * P;
       A[l * ldab + kv - (l - j)] = urow[idx];
     }
-    prev_tp = tp;
-    prev_nrows = nrows;
-    prev_pv = pv;
-    prev_rcp = rcp;
-    if (!pole_barrier(cnt, gen, (unsigned)P, my_gen, status)) return;
-  }
-  if (n > 0 && ((n - 1) % P) == b) {
-    cplx* cj = A + (n - 1) * ldab + kv;
-    for (int t = tid; t <= prev_nrows; t += T) cj[t] = (t == 0) ? prev_pv : mult[t];
-    if (tid == 0) {
-      pv_out[n - 1] = (int)(n - 1 + prev_tp);
-      di_out[n - 1] = prev_rcp;
-    }
+    __syncthreads();
   }
 }
 
+int band_lu_ring_slots(int q) {
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int pmax = sms / (q > 0 ? q : 1);
+  return 2 * (pmax > 1 ? pmax : 1) + 2;
+}
+
 cudaError_t launch_band_lu(int q, int64_t n, int kl, int ldab, int64_t n_pad, cplx* AB,
-                           int* piv, cplx* dinv, unsigned* bar, int* status, cudaStream_t s,
-                           int* ctas_per_pole) {
+                           int* piv, cplx* dinv, cplx* ring, int* ring_tp, unsigned* ring_flag,
+                           int R, int* status, cudaStream_t s, int* ctas_per_pole) {
   int dev = 0, sms = 0, per_sm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -294,7 +325,10 @@ cudaError_t launch_band_lu(int q, int64_t n, int kl, int ldab, int64_t n_pad, cp
   int P = sms / q;
   if (P < 1) P = 1;
   if (P > kv) P = kv;
-  if (P < 1) P = 1;
+  // a ring slot is rewritten R steps after its last reader could still need it: CTAs are at
+  // most P + 1 steps apart (the slowest one publishes the pivot of one of every P columns)
+  if (P > R - 2) P = R - 2;
+  if (P < 1) return cudaErrorInvalidValue;
   int nown_max = (kv + P - 1) / P + 1;
   size_t smem = (size_t)(2 * (kl + 1) + 2 * nown_max) * sizeof(cplx);
   if (smem > 48 * 1024) ie_smem_optin((const void*)band_lu_kernel);
@@ -306,8 +340,9 @@ cudaError_t launch_band_lu(int q, int64_t n, int kl, int ldab, int64_t n_pad, cp
   }
   smem = (size_t)(2 * (kl + 1) + 2 * nown_max) * sizeof(cplx);
   if (ctas_per_pole) *ctas_per_pole = P;
-  cudaMemsetAsync(bar, 0, sizeof(unsigned) * 2 * q, s);
-  void* args[] = {&n, &kl, &ldab, &n_pad, &AB, &piv, &dinv, &bar, &status, &P, &nown_max};
+  cudaMemsetAsync(ring_flag, 0, sizeof(unsigned) * (size_t)R * q, s);
+  void* args[] = {&n, &kl, &ldab, &n_pad, &AB, &piv, &dinv, &ring, &ring_tp, &ring_flag, &R,
+                  &status, &P, &nown_max};
   ie_count_launch();
   return cudaLaunchCooperativeKernel((void*)band_lu_kernel, dim3(q * P), dim3(512), args, smem, s);
 }

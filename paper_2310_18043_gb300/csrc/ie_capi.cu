@@ -97,7 +97,9 @@ struct ie_handle_s {
   zc sig() const { return side ? std::conj(sigma) : sigma; }
   double nA() const { return side ? normAH : normA; }
   double nB() const { return side ? normBH : normB; }
-  unsigned* bar = nullptr;
+  unsigned* bar = nullptr;     // band LU: ring flags (q * ring slots)
+  cplx* lu_ring = nullptr;     // band LU: published multipliers (q * slots * (kl + 1))
+  int* lu_ring_tp = nullptr;   // band LU: published pivot offsets
   int* status = nullptr;
   int lu_ctas = 0;
   // mixed precision (opts.precision = 1): complex64 factors and FP32-solve scratch
@@ -446,7 +448,9 @@ extern "C" ie_status ie_create(const ie_pencil* pen, ie_complex center, double r
   if (h->alloc(&h->AB, (size_t)q * h->n_pad * h->ldab) != cudaSuccess ||
       h->alloc(&h->piv, (size_t)q * h->n_pad) != cudaSuccess ||
       h->alloc(&h->dinv, (size_t)q * h->n_pad) != cudaSuccess ||
-      h->alloc(&h->bar, (size_t)2 * q) != cudaSuccess ||
+      h->alloc(&h->lu_ring, (size_t)q * band_lu_ring_slots(q) * (kl + 1)) != cudaSuccess ||
+      h->alloc(&h->lu_ring_tp, (size_t)q * band_lu_ring_slots(q)) != cudaSuccess ||
+      h->alloc(&h->bar, (size_t)q * band_lu_ring_slots(q)) != cudaSuccess ||
       h->alloc(&h->status, ST_COUNT) != cudaSuccess)
     return fail(IE_ERR_OOM);
   cudaMemsetAsync(h->status, 0, sizeof(int) * ST_COUNT, s);
@@ -457,7 +461,8 @@ extern "C" ie_status ie_create(const ie_pencil* pen, ie_complex center, double r
   cudaEventCreate(&e1);
   cudaEventRecord(e0, s);
   launch_assemble(h->P, h->d_poles, q, kl, h->ldab, h->n_pad, h->AB, s);
-  cudaError_t le = launch_band_lu(q, h->n, kl, h->ldab, h->n_pad, h->AB, h->piv, h->dinv, h->bar,
+  cudaError_t le = launch_band_lu(q, h->n, kl, h->ldab, h->n_pad, h->AB, h->piv, h->dinv,
+                                  h->lu_ring, h->lu_ring_tp, h->bar, band_lu_ring_slots(q),
                                   h->status, s, &h->lu_ctas);
   cudaEventRecord(e1, s);
   if (le != cudaSuccess) { cudaEventDestroy(e0); cudaEventDestroy(e1); return fail(map_err(le)); }

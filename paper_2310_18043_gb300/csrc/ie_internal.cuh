@@ -104,9 +104,11 @@ void launch_spmv(const DiaDev& P, cplx alphaA, cplx alphaB, const cplx* X, int64
 void launch_assemble(const DiaDev& P, const cplx* d_poles, int q, int kl, int ldab,
                      int64_t n_pad, cplx* AB, cudaStream_t s);
 // Batched band LU with partial pivoting, all q poles in one cooperative launch.
+// Ring slots per pole for the LU's published pivots (> the CTAs per pole it will use).
+int band_lu_ring_slots(int q);
 cudaError_t launch_band_lu(int q, int64_t n, int kl, int ldab, int64_t n_pad, cplx* AB,
-                           int* piv, cplx* dinv, unsigned* bar, int* status, cudaStream_t s,
-                           int* ctas_per_pole);
+                           int* piv, cplx* dinv, cplx* ring, int* ring_tp, unsigned* ring_flag,
+                           int R, int* status, cudaStream_t s, int* ctas_per_pole);
 // Forward (P, L) then backward (U) band solves for all q poles and k RHS columns;
 // Xp[i] (n x k, ld = ldx, pole stride xstride) = w_i K_i^{-1} RHS.
 // L64/U64: the split complex128 factors (launch_factors_split64); Tb/Hb/Ub: the per-panel
