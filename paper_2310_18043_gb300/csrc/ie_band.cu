@@ -177,17 +177,17 @@ __global__ void __launch_bounds__(512) band_lu_kernel(int64_t n, int kl, int lda
   __shared__ double red_v[32];
   __shared__ int red_i[32];
   __shared__ int s_tp;
-  __shared__ cplx s_u, s_a;
 
   // pivot search, multipliers, final column entries and publication of step jc (owner of
   // column jc only); column jc holds all updates of steps < jc in global memory
-  auto pivot_publish = [&](int64_t jc) {
+  // col[0..pre) already holds rows jc..jc+pre-1 of the column (the look-ahead update)
+  auto pivot_publish = [&](int64_t jc, int pre) {
     const int nr = (int)((n - 1 - jc) < (int64_t)kl ? (n - 1 - jc) : (int64_t)kl);
     cplx* cj = A + jc * ldab + kv;
     double best = -1.0;
     int bi = 0;
     for (int t = tid; t <= nr; t += T) {
-      const cplx v = __ldcg(cj + t);
+      const cplx v = (t < pre) ? col[t] : __ldcg(cj + t);
       col[t] = v;
       const double a = cabs1(v);
       if (a > best) { best = a; bi = t; }
@@ -234,7 +234,7 @@ __global__ void __launch_bounds__(512) band_lu_kernel(int64_t n, int kl, int lda
     }
   };
 
-  if (n > 0 && b == 0) pivot_publish(0);
+  if (n > 0 && b == 0) pivot_publish(0, 0);
   int64_t ju = 0;
   for (int64_t j = 0; j < n; ++j) {
     // (a) step j's pivot offset and multipliers, published by the owner of column j
@@ -248,18 +248,24 @@ __global__ void __launch_bounds__(512) band_lu_kernel(int64_t n, int kl, int lda
     // (b) look-ahead: the owner of column j+1 applies step j to it, then publishes step j+1
     const bool own_next = (j + 1 < n) && ((j + 1) % P == b);
     if (own_next) {
+      int pre = 0;
       if (j + 1 <= ju && nrows > 0) {
         cplx* cl = A + (j + 1) * ldab + kv - 1;      // row j of column j+1
-        if (tid == 0) { s_u = __ldcg(cl + tp); s_a = __ldcg(cl); }
-        __syncthreads();
-        const cplx u = s_u, a0 = s_a;
+        const cplx u = __ldcg(cl + tp), a0 = __ldcg(cl);
+        __syncthreads();                             // rows j and j+tp read before rewritten
         for (int t = tid; t <= nrows; t += T) {
-          if (t == 0) cl[0] = u;
-          else cl[t] = cfms(mult[t], u, (t == tp) ? a0 : __ldcg(cl + t));
+          if (t == 0) {
+            cl[0] = u;
+          } else {
+            const cplx nv = cfms(mult[t], u, (t == tp) ? a0 : __ldcg(cl + t));
+            cl[t] = nv;
+            col[t - 1] = nv;                         // row j+t = row (j+1)+(t-1) of the column
+          }
         }
+        pre = nrows;
         __syncthreads();
       }
-      pivot_publish(j + 1);
+      pivot_publish(j + 1, pre);
     }
     // (c) swap + rank-1 update of the other owned columns l in (j, ju], l % P == b
     const int64_t jn = own_next ? j + 2 : j + 1;    // column j+1 is done when owned here
