@@ -101,6 +101,17 @@ def test_status_strings_and_defaults(lib):
     o = ie.ie_opts_default()
     assert (o.k, o.driver, o.m_max, o.max_outer) == (16, 1, 100, 10)
     assert (o.tau_g, o.tau, o.gmres_tol, o.sigma_is_center) == (1e-2, 1e-10, 1e-12, 1)
+    assert (o.precision, o.refine_steps, o.adjoint) == (0, 2, 0)
+
+
+def test_argument_checks_need_no_gpu(lib):
+    """Entry points reject invalid arguments before any CUDA call, so these run on a host
+    without a GPU: a NULL handle, an empty batch."""
+    import paper_2310_18043_gb300.ie as ie
+    assert ie.ie_destroy(None) == ie.IE_ERR_ARG
+    st, _ = ie.ie_solve_batch([])
+    assert st == ie.IE_ERR_ARG
+    assert ie.load().ie_solve_batch(None, 3, 0) == ie.IE_ERR_ARG
 
 
 def test_no_oracle_in_product_path():
