@@ -168,13 +168,14 @@ __global__ void __maxnreg__(REGS) band_solve_kernel(SolveArgsT<CT> a) {
       const int s = tid + u * T;
       mem[u] = -1;
       if (s >= Sf) continue;
-      const int64_t r = frow[u];
-      if (r >= j0 && r < j0 + NB) {
-        mem[u] = (int)(r - j0);
+      const int dr = (int)(frow[u] - j0);   // row offset from the panel head (32-bit)
+      if (dr >= 0 && dr < NB) {
+        mem[u] = dr;
       } else {
+        const int j0i = (int)j0;
 #pragma unroll
         for (int i = NB; i < 16; ++i)
-          if (Hst[i] == r) mem[u] = i;
+          if (Hst[i] - j0i == dr) mem[u] = i;
       }
       if (mem[u] >= 0)
 #pragma unroll
@@ -215,11 +216,12 @@ __global__ void __maxnreg__(REGS) band_solve_kernel(SolveArgsT<CT> a) {
 #pragma unroll
         for (int c = 0; c < NC; ++c) v[u][c] = hv2[i * NC + c];
       } else {
+        const int dr = (int)(r - j0);           // 32-bit offsets inside the window
 #pragma unroll
         for (int jj = 0; jj < NB; ++jj) {
-          const int64_t j = j0 + jj;
-          if (jj < nvalid && r > j && r <= j + kl) {
-            const CT lv = Lst[(size_t)jj * klp + (r - j - 1)];
+          const int dd = dr - jj;               // row - (j0 + jj)
+          if (jj < nvalid && dd > 0 && dd <= kl) {
+            const CT lv = Lst[jj * klp + dd - 1];
 #pragma unroll
             for (int c = 0; c < NC; ++c) v[u][c] = cfms(lv, hv2[jj * NC + c], v[u][c]);
           }
