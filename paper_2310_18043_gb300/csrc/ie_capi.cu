@@ -3,6 +3,8 @@
 // SIsketch) and the two drivers (Alg. 1, Alg. 2). Host code orchestrates kernels on one stream;
 // the GMRES loop reads k residuals back per Arnoldi step for its convergence test.
 #include <algorithm>
+#include <cstdio>
+#include <cstdlib>
 #include <cmath>
 #include <complex>
 #include <cstring>
@@ -920,6 +922,15 @@ extern "C" ie_status ie_hsrr(ie_handle h, const ie_complex* U_any, int64_t ldu, 
 }
 
 // ------------------------------ drivers ----------------------------------------------------------
+// IE_SOLVE_LOG=1: one line per outer iteration of the drivers on stderr
+static bool solve_log() {
+  static const bool on = [] {
+    const char* v = getenv("IE_SOLVE_LOG");
+    return v && v[0] == '1';
+  }();
+  return on;
+}
+
 static bool in_disk(ie_handle h, zc l) {
   return std::isfinite(l.real()) && std::isfinite(l.imag()) && std::abs(l - h->ctr()) < h->radius;
 }
@@ -991,6 +1002,18 @@ static ie_status solve_driver(ie_handle h, const ie_complex* Y0_any, int64_t ldy
         mr = std::max(mr, rho[i]);
         if (!(rho[i] < h->opts.tau)) all_conv = false;
       }
+    }
+    if (solve_log()) {
+      int unconv = 0, inside = 0;
+      double emax = 0.0;
+      for (int i = 0; i < k; ++i) {
+        if (filt[i] && !(rho[i] < h->opts.tau)) ++unconv;
+        if (in_disk(h, lam[i])) ++inside;
+        if (filt[i]) emax = std::max(emax, e[i]);
+      }
+      fprintf(stderr, "ie_solve%s t=%d p=%d: Ritz values in D %d, filtered %d, not yet converged %d, "
+              "max rho %.3e, max e %.3e, gmres steps %d..%d\n", h->side ? " (adjoint)" : "", t,
+              pc, inside, nf, unconv, mr, emax, h->stats.gmres_iters_min, h->stats.gmres_iters_max);
     }
     S.outer_iters = t;
     S.n_found = nf;
