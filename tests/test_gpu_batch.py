@@ -73,3 +73,27 @@ def test_batch_rejects_shared_handles_and_empty(ie):
         assert st == ie.IE_ERR_ARG
     finally:
         c.close()
+
+
+def test_mixed_precision_batch_equals_individual_solves(ie):
+    """The batch with mixed-precision handles (complex64 factors, FP64 refinement): each item
+    equals its one-at-a-time ie_solve and matches the reference eigenvalues at rho <= 1e-10."""
+    names = ["m1_m64", "b0_m64_d0", "b2_m96_d0"]
+    cases = [Case(ie, nm, precision=1) for nm in names]
+    try:
+        probs = [(c.h, dblock(_start(c)), dzeros(c.n, c.w["k"]), c.w["k"]) for c in cases]
+        st, res = ie.ie_solve_batch(probs, max_workers=3)
+        assert st == ie.IE_OK, [ie.ie_status_str(r["status"]) for r in res]
+        for c, r in zip(cases, res):
+            nf = r["n_found"]
+            ref = golden_eigs(c.w)
+            assert nf == len(ref)
+            match_eigs(r["lam"][:nf], ref)
+            assert np.all(r["rho"][:nf] <= 1e-10)
+            k = c.w["k"]
+            st1, lam1, _, _, nf1, _ = ie.ie_solve(c.h, dblock(_start(c)), dzeros(c.n, k), k)
+            assert st1 == ie.IE_OK and nf1 == nf
+            assert np.max(np.abs(lam1[:nf] - r["lam"][:nf]) / np.abs(lam1[:nf])) < 1e-12
+    finally:
+        for c in cases:
+            c.close()
