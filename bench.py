@@ -160,6 +160,18 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------ native arm
+def workload_config(name, world):
+    """The workload description shared by both arms (static: no measured values)."""
+    import ie_inputs
+    w = ie_inputs.load_workload(name)
+    n = w["m"] * w["m"]
+    return {"workload": f"{name}: m={w['m']} convection-diffusion pencil, n={n}, band {w['m']}, "
+                        f"q={w['q']}, p={w['p']}, k={w['k']}, disk with "
+                        f"{len(w['eig_in_disk_re'])} eigenvalues",
+            "n": n, "q": w["q"], "p": w["p"], "k": w["k"], "parallelism": f"replicas x{world}",
+            "l2": "no flush: the factors and Krylov bases exceed L2"}
+
+
 def run_native(args):
     import torch
 
@@ -349,15 +361,12 @@ def run_native(args):
             "scaling": "weak", "vs_baseline": None,
             "dtype": "c128" if args.precision == 0 else "c64 solves + f64 refinement",
             "data": "synthetic",
-            "config": {"workload": f"{args.workload}: m={w['m']} convection-diffusion pencil, "
-                                   f"n={n}, band {pen.half_bw}, q={q}, p={p}, k={k}, "
-                                   f"disk with {len(w['eig_in_disk_re'])} eigenvalues",
-                       "n": n, "q": q, "p": p, "k": k, "parallelism": f"replicas x{world}",
-                       "l2": "no flush: factors (6.45 GB) and Krylov bases exceed L2",
-                       "factor_ms": s0["t_factor_ms"], "create_s": create_s,
-                       "gmres_iters_max": last["gmres"],
-                       "ritz_in_disk": int(inside.sum()),
-                       "ritz_in_disk_rho_max": float(np.max(last["rho"][inside])) if inside.any() else None},
+            "config": workload_config(args.workload, world),
+            "details": {"factor_ms": s0["t_factor_ms"], "create_s": create_s,
+                        "gmres_iters_max": last["gmres"],
+                        "ritz_in_disk": int(inside.sum()),
+                        "ritz_in_disk_rho_max": (float(np.max(last["rho"][inside]))
+                                                 if inside.any() else None)},
             "roofline": {"bound": "alu",
                          "kernel": "band_solve_kernel (%s complex band solves)"
                                    % ("FP64" if args.precision == 0 else "FP32"),
@@ -664,8 +673,8 @@ def run_reference(args):
                                            "composite filter + HSRR)",
             "value": v, "unit": "filtered columns/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": wall * 1e3 / max(args.steps, 1),
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": args.workload},
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128",
+            "data": "synthetic", "config": workload_config(args.workload, world),
             "cpu_baseline": {"value": v, "unit": "filtered columns/s", "cores": 1,
                              "kind": "oracle", "sample": cb["sample"] if vals else None},
             "e2e": {"value": v, "unit": "filtered columns/s", "h2d_bytes_per_step": 0,
