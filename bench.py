@@ -165,11 +165,14 @@ def workload_config(name, world):
     import ie_inputs
     w = ie_inputs.load_workload(name)
     n = w["m"] * w["m"]
+    fbytes = w["q"] * n * (3 * w["m"] + 1) * 16
     return {"workload": f"{name}: m={w['m']} convection-diffusion pencil, n={n}, band {w['m']}, "
                         f"q={w['q']}, p={w['p']}, k={w['k']}, disk with "
                         f"{len(w['eig_in_disk_re'])} eigenvalues",
             "n": n, "q": w["q"], "p": w["p"], "k": w["k"], "parallelism": f"replicas x{world}",
-            "l2": "no flush: the factors and Krylov bases exceed L2"}
+            "l2": (f"no flush: the factors ({fbytes / 1e9:.2f} GB) exceed the 129 MB L2"
+                   if fbytes > 129e6 else
+                   f"factors ({fbytes / 1e6:.0f} MB) fit in L2: a parity-size workload")}
 
 
 def run_native(args):
