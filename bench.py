@@ -597,6 +597,19 @@ def time_left_and_gradient(ie, w, pen, A_d, B_d, device, stream, Xd, out):
                 "adjoint_outer_iters": sst["outer_iters"],
                 "gradient_ms": e0.elapsed_time(e1),
                 "grad_norm": float(torch.linalg.vector_norm(grad).item())})
+    # the complex64 conjugate-transpose kernel on k columns (1 solve + refinement solves)
+    V = torch.from_numpy(np.ascontiguousarray(ie_inputs.random_block(n, k, seed=3).T)).to(device).T
+    GV = torch.zeros((k, n), dtype=torch.complex128, device=device).T
+    ie.ie_apply_GH(h, V, GV, stream)
+    torch.cuda.synchronize()
+    _, a0 = ie.ie_get_stats(h)
+    for _ in range(3):
+        ie.ie_apply_GH(h, V, GV, stream)
+    torch.cuda.synchronize()
+    _, a1 = ie.ie_get_stats(h)
+    la = a1["adj_launches"] - a0["adj_launches"]
+    ms = a1["t_adj_ms"] - a0["t_adj_ms"]
+    out["band_solve_adj_c64"] = {"k": k, "launches": la, "avg_launch_ms": ms / la if la else None}
     ie.ie_destroy(h)
 
 

@@ -379,6 +379,19 @@ __global__ void __maxnreg__(REGS) band_solve_adj_kernel(AdjArgsT<CT> a) {
       win[(int)(r % S2) * NC + c] = (r < n && c < ncol) ? Yo[(int64_t)(c0 + c) * a.ldy + r] : zero;
     }
   }
+  // the 8 rows entering the window at a panel's (C) are loaded one panel ahead, in registers
+  // (NB * NC <= 64 <= 2 * T items, at most two per thread)
+  CT pf[2];
+#pragma unroll
+  for (int i = 0; i < 2; ++i) {
+    const int e = tid + i * T;
+    pf[i] = zero;
+    if (e < NB * NC) {
+      const int t = e / NC, c = e - (e / NC) * NC;
+      const int64_t r2 = a.n_pad - 2 * NB + t;
+      if (r2 >= 0 && c < ncol) pf[i] = Yo[(int64_t)(c0 + c) * a.ldy + r2];
+    }
+  }
   // dot products: groups of g lanes (a power of two within a warp)
   int g = 32;
   while (g > 1 && g * NB * NC > T) g >>= 1;
@@ -444,13 +457,17 @@ __global__ void __maxnreg__(REGS) band_solve_adj_kernel(AdjArgsT<CT> a) {
     if (tid < NB && Hst[NB + tid] >= 0) mflag[Hst[NB + tid] % S2] = 0;
     __syncthreads();
     // (C) rows j0+kl .. j0+kl+7 are final: write them; rows j0-8 .. j0-1 enter their slots
-    for (int e = tid; e < NB * NC; e += T) {
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+      const int e = tid + i * T;
+      if (e >= NB * NC) continue;
       const int t = e / NC, c = e - (e / NC) * NC;
       const int64_t r = j0 + kl + t;
       const int sl = (int)(r % S2);
       if (r < n && c < ncol) out(r, c, win[sl * NC + c]);
-      const int64_t r2 = j0 - NB + t;
-      win[sl * NC + c] = (r2 >= 0 && c < ncol) ? Yo[(int64_t)(c0 + c) * a.ldy + r2] : zero;
+      win[sl * NC + c] = pf[i];                       // row j0 - NB + t (zero if < 0)
+      const int64_t r3 = j0 - 2 * NB + t;             // entering row of the next panel
+      pf[i] = (r3 >= 0 && c < ncol) ? Yo[(int64_t)(c0 + c) * a.ldy + r3] : zero;
     }
     __syncthreads();
   }
