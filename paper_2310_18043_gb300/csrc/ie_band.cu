@@ -8,6 +8,8 @@
 
 #include <atomic>
 
+#include <cstdlib>
+
 #include "ie_internal.cuh"
 
 static std::atomic<int64_t> g_launches{0};
@@ -159,7 +161,7 @@ __global__ void __launch_bounds__(512) band_lu_kernel(int64_t n, int kl, int lda
                                                       cplx* AB, int* piv, cplx* dinv,
                                                       cplx* ring, int* ring_tp,
                                                       unsigned* ring_flag, int R, int* status,
-                                                      int P, int nown_max) {
+                                                      int P, int nown_max, int64_t skip_publish) {
   const int pole = blockIdx.x / P, b = blockIdx.x % P;
   const int T = blockDim.x, tid = threadIdx.x;
   const int kv = 2 * kl;
@@ -228,7 +230,7 @@ __global__ void __launch_bounds__(512) band_lu_kernel(int64_t n, int kl, int lda
       rtp[jc % R] = tp;
     }
     __syncthreads();
-    if (tid == 0) {
+    if (tid == 0 && jc != skip_publish) {   // skip_publish: failure test hook (normally -1)
       __threadfence();
       st_release_u32(rflag + (jc % R), (unsigned)(jc + 1));
     }
@@ -347,8 +349,13 @@ cudaError_t launch_band_lu(int q, int64_t n, int kl, int ldab, int64_t n_pad, cp
   smem = (size_t)(2 * (kl + 1) + 2 * nown_max) * sizeof(cplx);
   if (ctas_per_pole) *ctas_per_pole = P;
   cudaMemsetAsync(ring_flag, 0, sizeof(unsigned) * (size_t)R * q, s);
+  // Failure test hook: IE_TEST_SKIP_PUBLISH=j makes the owner of column j never set its flag,
+  // so every CTA's bounded wait for step j runs out (IE_WAIT_NS), the kernel records a
+  // timeout and returns, and ie_create reports IE_ERR_TIMEOUT. Nothing faults or hangs.
+  int64_t skip_publish = -1;
+  if (const char* e = getenv("IE_TEST_SKIP_PUBLISH")) skip_publish = atoll(e);
   void* args[] = {&n, &kl, &ldab, &n_pad, &AB, &piv, &dinv, &ring, &ring_tp, &ring_flag, &R,
-                  &status, &P, &nown_max};
+                  &status, &P, &nown_max, &skip_publish};
   ie_count_launch();
   return cudaLaunchCooperativeKernel((void*)band_lu_kernel, dim3(q * P), dim3(512), args, smem, s);
 }
