@@ -122,3 +122,24 @@ def test_no_oracle_in_product_path():
             if f.endswith((".py", ".cu", ".cuh", ".h")):
                 txt = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in txt and "from oracle" not in txt, f
+
+
+def test_block_marshalling_reads_column_major_layouts():
+    """The binding passes a block as (pointer, leading dimension, rows, columns) and accepts
+    only column-major complex128 blocks (numpy Fortran order or a transposed torch tensor)."""
+    import numpy as np
+    import paper_2310_18043_gb300.ie as ie
+    a = np.zeros((10, 3), dtype=np.complex128, order="F")
+    p, ld, n, k = ie._block(a)
+    assert (ld, n, k) == (10, 10, 3) and p.value == a.ctypes.data
+    big = np.zeros((13, 3), dtype=np.complex128, order="F")
+    p, ld, n, k = ie._block(big[:10])                     # ragged leading dimension
+    assert (ld, n, k) == (13, 10, 3)
+    with pytest.raises(ValueError):
+        ie._block(np.zeros((10, 3), dtype=np.complex128))  # row-major
+    with pytest.raises(TypeError):
+        ie._block(np.zeros((10, 3), dtype=np.complex64, order="F"))
+    torch = pytest.importorskip("torch")
+    t = torch.zeros((3, 10), dtype=torch.complex128).T     # n x k view of a (k, n) tensor
+    p, ld, n, k = ie._block(t)
+    assert (ld, n, k) == (10, 10, 3)
