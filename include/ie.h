@@ -204,14 +204,18 @@ ie_status ie_get_stats(ie_handle h, ie_stats* out);
  * and the q per-pole solve buffers) lives in one file-scope device array of
  * IE_STATIC_SCRATCH_BYTES bytes, which every GPU that loads the library keeps until the
  * process exits. Limit: (q + 1) * n * k * 16 <= IE_STATIC_SCRATCH_BYTES, else
- * IE_ERR_SCRATCH_LIMIT (nothing is launched). Complex128 handles only (precision = 0;
- * IE_ERR_ARG otherwise). d_V, d_GV: device pointers, n x k, ld >= n;
- * the current device must be the handle's. The first call on a device looks up the array's
- * device address (cudaGetSymbolAddress) once for that device; make that first call before
- * any stream capture. All calls in the process share the one array: calls whose work
- * overlaps on the GPU (different streams or threads, any handles) race on it and must be
- * serialised by the caller. Every scratch element a call reads is first written by the
- * same call, so nothing needs clearing between calls. */
+ * IE_ERR_SCRATCH_LIMIT (nothing is launched). k may exceed opts.k within that limit.
+ * Complex128 handles only (precision = 0; IE_ERR_ARG otherwise). d_V, d_GV: device (or
+ * managed) memory of the handle's GPU, n x k, ld >= n; the current device must be the
+ * handle's (IE_ERR_ARG otherwise). The first call on a device looks up the array's device
+ * address (cudaGetSymbolAddress) once for that device; under CUDA's lazy module loading
+ * that first call also loads the module that holds the array, which is when the device
+ * reserves its IE_STATIC_SCRATCH_BYTES. Make that first call before any stream capture.
+ * Every call synchronises its stream before returning (it reads the kernels' status word).
+ * All calls in the process share the one array: calls whose work overlaps on the GPU
+ * (different streams or threads, any handles) race on it and must be serialised by the
+ * caller. Every scratch element a call reads is first written by the same call, so nothing
+ * needs clearing between calls. */
 #define IE_STATIC_SCRATCH_BYTES (32u * 1024u * 1024u)
 ie_status ie_apply_G_static(ie_handle h, const ie_complex* d_V, int64_t ldv, int32_t k,
                             ie_complex* d_GV, int64_t ldgv, void* stream);

@@ -32,13 +32,15 @@ cudaError_t scratch_ptr_for(int dev, cplx** out) {
   return cudaSuccess;
 }
 
-bool on_device(const void* p) {
+// Device memory of GPU `dev` itself (a block on another GPU would be read through a peer
+// mapping), or managed memory.
+bool on_device(const void* p, int dev) {
   cudaPointerAttributes at;
   if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
     cudaGetLastError();
     return false;
   }
-  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+  return at.type == cudaMemoryTypeManaged || (at.type == cudaMemoryTypeDevice && at.device == dev);
 }
 }  // namespace
 
@@ -50,7 +52,7 @@ extern "C" ie_status ie_apply_G_static(ie_handle h, const ie_complex* d_V, int64
   if (!f.L64 || !f.U64) return IE_ERR_ARG;   // complex128 handles only (precision = 0)
   int cur = -1;
   if (cudaGetDevice(&cur) != cudaSuccess || cur != f.dev) return IE_ERR_ARG;
-  if (!on_device(d_V) || !on_device(d_GV)) return IE_ERR_ARG;
+  if (!on_device(d_V, f.dev) || !on_device(d_GV, f.dev)) return IE_ERR_ARG;
   // scratch: B V (n x k) followed by the q per-pole solve buffers (n x k each)
   const unsigned long long need =
       (unsigned long long)(f.q + 1) * (unsigned long long)f.n * (unsigned long long)k;

@@ -160,6 +160,41 @@ def _block(x):
     raise TypeError(f"unsupported block type {type(x)}")
 
 
+# Matrix size n of every live handle (recorded by ie_create), so that the wrappers can check
+# block shapes before the library writes n x k outputs through raw pointers.
+_handle_n: dict = {}
+
+
+def _hkey(h):
+    return h.value if isinstance(h, C.c_void_p) else h
+
+
+def _check_rows(h, rows, where):
+    n = _handle_n.get(_hkey(h))
+    if n is not None and rows != n:
+        raise ValueError(f"{where}: block has {rows} rows, the handle's matrix size is {n}")
+
+
+def _in_out(h, X, Y, where):
+    """Input X and output Y of an n x k -> n x k call: (px, ldx, k, py, ldy). Raises
+    ValueError unless Y has exactly X's shape and both have the handle's n rows."""
+    px, ldx, n, k = _block(X)
+    py, ldy, ny, ky = _block(Y)
+    _check_rows(h, n, where)
+    if (ny, ky) != (n, k):
+        raise ValueError(f"{where}: output block is {ny} x {ky}, input block is {n} x {k}")
+    return px, ldx, k, py, ldy
+
+
+def _out_cols(h, X, cols, where):
+    """An output block that receives `cols` columns: (pointer, ld)."""
+    px, ldx, n, k = _block(X)
+    _check_rows(h, n, where)
+    if k < cols:
+        raise ValueError(f"{where}: output block has {k} columns, {cols} are written")
+    return px, ldx
+
+
 def _vec(x):
     if x is None:
         return None
@@ -190,43 +225,44 @@ def ie_create(n, offsets, A_dia, B_dia, center, radius, p, q, opts=None, stream=
     o = opts if opts is not None else ie_opts_default()
     st = L.ie_create(C.byref(pen), ie_complex(complex(center).real, complex(center).imag),
                      float(radius), int(p), int(q), C.byref(o), _stream(stream), C.byref(h))
+    if h.value:
+        _handle_n[h.value] = int(n)
     return st, h
 
 
 def ie_destroy(h):
+    if h is not None:
+        _handle_n.pop(_hkey(h), None)
     return load().ie_destroy(h)
 
 
 def ie_filter_apply(h, Y, U, stream=None):
-    py, ldy, n, k = _block(Y)
-    pu, ldu, _, _ = _block(U)
+    py, ldy, k, pu, ldu = _in_out(h, Y, U, "ie_filter_apply")
     return load().ie_filter_apply(h, py, ldy, k, pu, ldu, _stream(stream))
 
 
 def ie_apply_G(h, V, GV, stream=None):
-    pv, ldv, n, k = _block(V)
-    pg, ldg, _, _ = _block(GV)
+    pv, ldv, k, pg, ldg = _in_out(h, V, GV, "ie_apply_G")
     return load().ie_apply_G(h, pv, ldv, k, pg, ldg, _stream(stream))
 
 
 def ie_apply_G_static(h, V, GV, stream=None):
     """G(V) with the library's static scratch: no device allocation by the call.
     V, GV must be device tensors."""
-    pv, ldv, n, k = _block(V)
-    pg, ldg, _, _ = _block(GV)
+    pv, ldv, k, pg, ldg = _in_out(h, V, GV, "ie_apply_G_static")
     return load().ie_apply_G_static(h, pv, ldv, k, pg, ldg, _stream(stream))
 
 
 def ie_spmv(h, which, X, Y, stream=None):
-    px, ldx, n, k = _block(X)
-    py, ldy, _, _ = _block(Y)
+    px, ldx, k, py, ldy = _in_out(h, X, Y, "ie_spmv")
     return load().ie_spmv(h, int(which), px, ldx, k, py, ldy, _stream(stream))
 
 
 def ie_hsrr(h, U, X=None, stream=None):
     """Returns (status, lambda (k,), e (k,), rho (k,)); Ritz vectors into X when given."""
     pu, ldu, n, k = _block(U)
-    px, ldx, _, _ = _block(X)
+    _check_rows(h, n, "ie_hsrr")
+    px, ldx = _out_cols(h, X, k, "ie_hsrr") if X is not None else (None, 0)
     lam = np.zeros(k, dtype=np.complex128)
     e = np.zeros(k)
     rho = np.zeros(k)
@@ -237,8 +273,12 @@ def ie_hsrr(h, U, X=None, stream=None):
 
 def ie_solve(h, Y0, X, k, stream=None):
     """Returns (status, lambda (k,), rho (k,), e (k,), n_found, stats dict)."""
-    p0, ld0, _, _ = _block(Y0)
-    px, ldx, _, _ = _block(X)
+    p0, ld0, n0, k0 = _block(Y0)
+    if Y0 is not None:
+        _check_rows(h, n0, "ie_solve")
+        if k0 < k:
+            raise ValueError(f"ie_solve: starting block has {k0} columns, {k} are read")
+    px, ldx = _out_cols(h, X, k, "ie_solve")
     lam = np.zeros(k, dtype=np.complex128)
     rho = np.zeros(k)
     e = np.zeros(k)
@@ -251,8 +291,7 @@ def ie_solve(h, Y0, X, k, stream=None):
 
 def ie_apply_GH(h, V, GV, stream=None):
     """GV = sum_i conj(w_i) K_i^{-H} B^H V (handles created with opts.adjoint = 1)."""
-    pv, ldv, n, k = _block(V)
-    pg, ldg, _, _ = _block(GV)
+    pv, ldv, k, pg, ldg = _in_out(h, V, GV, "ie_apply_GH")
     return load().ie_apply_GH(h, pv, ldv, k, pg, ldg, _stream(stream))
 
 
@@ -261,8 +300,10 @@ def ie_solve_left(h, lam, Y, Y0=None, stream=None):
     Returns (status, lambda_left (nl,), rho_left (nl,), stats dict)."""
     lam = np.ascontiguousarray(np.asarray(lam, dtype=np.complex128))
     nl = len(lam)
-    p0, ld0, _, _ = _block(Y0)
-    py, ldy, _, _ = _block(Y)
+    p0, ld0, n0, _ = _block(Y0)
+    if Y0 is not None:
+        _check_rows(h, n0, "ie_solve_left")
+    py, ldy = _out_cols(h, Y, nl, "ie_solve_left")
     ll = np.zeros(nl, dtype=np.complex128)
     rl = np.zeros(nl)
     stt = ie_stats()
@@ -274,12 +315,17 @@ def ie_solve_left(h, lam, Y, Y0=None, stream=None):
 def ie_eig_sensitivity(h, X, Y, alpha=1j, S=None, gbar=None, grad=None, stream=None):
     """S[j, i] = alpha conj(Y[j, i]) X[j, i] / (Y_i^H B X_i) into S (n x nf) and
     grad[j] = Re sum_i conj(gbar_i) S[j, i] into grad (n doubles); either may be None."""
-    px, ldx, n, nf = _block(X)
-    py, ldy, _, _ = _block(Y)
-    ps, lds, _, _ = _block(S)
+    px, ldx, nf, py, ldy = _in_out(h, X, Y, "ie_eig_sensitivity")
+    ps, lds = _out_cols(h, S, nf, "ie_eig_sensitivity") if S is not None else (None, 0)
     gb = None
     if gbar is not None:
         gb = np.ascontiguousarray(np.asarray(gbar, dtype=np.complex128))
+        if gb.shape != (nf,):
+            raise ValueError(f"ie_eig_sensitivity: gbar has shape {gb.shape}, expected ({nf},)")
+    if grad is not None:
+        n = _handle_n.get(_hkey(h), grad.shape[0])
+        if tuple(grad.shape) != (n,) or "float64" not in str(grad.dtype):
+            raise ValueError(f"ie_eig_sensitivity: grad must be a vector of {n} float64 values")
     a = complex(alpha)
     return load().ie_eig_sensitivity(h, px, ldx, py, ldy, nf, ie_complex(a.real, a.imag), ps,
                                      lds if S is not None else 0, _vec(gb), _vec(grad),
@@ -293,8 +339,12 @@ def ie_solve_batch(problems, max_workers=0, streams=None):
     items = (ie_batch_item * nb)()
     keep = []
     for i, (h, Y0, X, k) in enumerate(problems):
-        p0, ld0, _, _ = _block(Y0)
-        px, ldx, _, _ = _block(X)
+        p0, ld0, n0, k0 = _block(Y0)
+        if Y0 is not None:
+            _check_rows(h, n0, "ie_solve_batch")
+            if k0 < k:
+                raise ValueError(f"ie_solve_batch: item {i} starting block has {k0} columns")
+        px, ldx = _out_cols(h, X, k, f"ie_solve_batch item {i}")
         lam = np.zeros(k, dtype=np.complex128)
         rho = np.zeros(k)
         e = np.zeros(k)

@@ -143,3 +143,37 @@ def test_block_marshalling_reads_column_major_layouts():
     t = torch.zeros((3, 10), dtype=torch.complex128).T     # n x k view of a (k, n) tensor
     p, ld, n, k = ie._block(t)
     assert (ld, n, k) == (10, 10, 3)
+
+
+def test_binding_rejects_output_blocks_of_the_wrong_shape():
+    """The library writes n x k outputs through raw pointers, with k and the leading
+    dimension taken from the input block. The binding refuses, before any library call, an
+    output narrower or shorter than the input, a 1-D output for k > 1, and blocks whose row
+    count differs from the handle's n."""
+    import numpy as np
+    import paper_2310_18043_gb300.ie as ie
+    h = 0x5EED                                    # a handle value the binding has seen created
+    ie._handle_n[h] = 10
+    try:
+        V = np.zeros((10, 3), dtype=np.complex128, order="F")
+        for bad in (np.zeros((10, 2), dtype=np.complex128, order="F"),
+                    np.zeros(10, dtype=np.complex128),
+                    np.zeros((9, 3), dtype=np.complex128, order="F")):
+            for fn in (ie.ie_apply_G, ie.ie_apply_G_static, ie.ie_apply_GH, ie.ie_filter_apply):
+                with pytest.raises(ValueError):
+                    fn(h, V, bad)
+            with pytest.raises(ValueError):
+                ie.ie_spmv(h, 0, V, bad)
+        short = np.zeros((11, 3), dtype=np.complex128, order="F")
+        with pytest.raises(ValueError):
+            ie.ie_apply_G(h, short, short)        # rows differ from the handle's n
+        with pytest.raises(ValueError):
+            ie.ie_hsrr(h, V, np.zeros((10, 2), dtype=np.complex128, order="F"))
+        with pytest.raises(ValueError):
+            ie.ie_solve(h, None, np.zeros((10, 2), dtype=np.complex128, order="F"), 3)
+        with pytest.raises(ValueError):
+            ie.ie_solve_left(h, np.ones(3), np.zeros((10, 2), dtype=np.complex128, order="F"))
+        with pytest.raises(ValueError):
+            ie.ie_eig_sensitivity(h, V, V, 1j, None, np.ones(3), np.zeros(9))
+    finally:
+        ie._handle_n.pop(h, None)

@@ -53,6 +53,42 @@ def test_static_scratch_matches_apply_G_on_consecutive_calls(handle):
         assert err < 1e-11, (call, err)
 
 
+def test_static_scratch_allocates_nothing(handle):
+    """After the first call (which, under lazy module loading, loads the module that holds
+    the array), further calls leave the device's free memory unchanged."""
+    ie, h, n, w = handle
+    k = w["k"]
+    V = _dev(ie_inputs.random_block(n, k, seed=33))
+    GV = _zeros(n, k)
+    assert ie.ie_apply_G_static(h, V, GV) == ie.IE_OK
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    for _ in range(3):
+        assert ie.ie_apply_G_static(h, V, GV) == ie.IE_OK
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0, (free0, free1)
+
+
+@pytest.mark.parametrize("extra", [None, 8])
+def test_static_scratch_other_block_widths(handle, extra):
+    """k = 1, and k wider than the handle's opts.k (allowed while (q+1) n k fits the array):
+    each column equals ie_apply_G on slices of at most opts.k columns."""
+    ie, h, n, w = handle
+    k = 1 if extra is None else w["k"] + extra
+    assert (w["q"] + 1) * n * k * 16 <= ie.IE_STATIC_SCRATCH_BYTES
+    V = _dev(ie_inputs.random_block(n, k, seed=40 + k))
+    got = _zeros(n, k)
+    assert ie.ie_apply_G_static(h, V, got) == ie.IE_OK
+    ref = _zeros(n, k)
+    for c0 in range(0, k, w["k"]):
+        c1 = min(k, c0 + w["k"])
+        assert ie.ie_apply_G(h, V[:, c0:c1], ref[:, c0:c1]) == ie.IE_OK
+    torch.cuda.synchronize()
+    err = (torch.linalg.norm(got - ref, dim=0) / torch.linalg.norm(ref, dim=0)).max().item()
+    assert err < 1e-11, err
+
+
 def test_static_scratch_rejects_oversized_problem(handle):
     ie, h, n, w = handle
     k = ie.IE_STATIC_SCRATCH_BYTES // (16 * (w["q"] + 1) * n) + 1
