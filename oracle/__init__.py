@@ -21,6 +21,9 @@ Pins (tests/test_oracle_*.py), each against something other than the oracle:
   adjoint  - dense spectral definition for the adjoint pencil; the identity
              B^H G_adj = G^H B^H; LAPACK left eigenvectors; central finite
              differences of dense eigenvalues for the sensitivities and the VJP.
+  reference_eigs - shift-invert Arnoldi against dense QZ on the m = 12 and m = 24
+             pencils; median and radius against hand-built arrays with ties and the
+             exact-count property (tests/test_oracle_reference_eigs.py).
 No function is "parity unpinned".
 """
 from . import coeffs, pencil, inner, msgmres, hsrr, drivers, adjoint  # noqa: F401

@@ -2,6 +2,7 @@
 term, a transposed operand) is caught by one of the pins. The mistakes are planted
 in the oracle on the CPU with monkeypatch; the pins are the functions of the pin tests."""
 import numpy as np
+import pytest
 
 import ie_inputs
 from oracle import coeffs, inner, msgmres, pencil
@@ -150,3 +151,60 @@ def test_denominator_without_b_is_caught(monkeypatch):
         return alpha * np.conj(Y) * X / den[None, :]
     monkeypatch.setattr(adjoint, "diag_sensitivity", bad)
     assert _sensitivity_error() > 1e-3
+
+
+# ---------------------------------------------------------------- reference eigenvalues
+from oracle import reference_eigs
+from test_oracle_reference_eigs import nearest_error
+
+
+def test_reference_eigs_pin_passes_unmutated():
+    assert nearest_error(12, 0, 10, 0.37 + 0.11j) < 1e-12
+
+
+def _bad_nearest(sign, which):
+    import scipy.sparse.linalg as spla
+
+    def bad(A, B, sigma, count, tol=1e-14, seed=0):
+        n = A.shape[0]
+        lu = spla.splu((A - sigma * B).tocsc())
+        op = spla.LinearOperator((n, n), matvec=lambda x: lu.solve(B @ x), dtype=np.complex128)
+        v0 = np.random.default_rng(seed).standard_normal(n).astype(np.complex128)
+        theta = spla.eigs(op, k=count, which=which, tol=tol, v0=v0, ncv=max(2 * count + 1, 40),
+                          return_eigenvectors=False)
+        lam = sigma + sign / theta
+        return lam[np.argsort(np.abs(lam - sigma))]
+    return bad
+
+
+def test_wrong_shift_invert_sign_is_caught(monkeypatch):
+    monkeypatch.setattr(reference_eigs, "nearest_eigenvalues", _bad_nearest(-1.0, "LM"))
+    assert nearest_error(12, 0, 10, 0.37 + 0.11j) > 1e-3
+
+
+def test_wrong_end_of_spectrum_is_caught(monkeypatch):
+    from scipy.sparse.linalg import ArpackNoConvergence
+    monkeypatch.setattr(reference_eigs, "nearest_eigenvalues", _bad_nearest(1.0, "SM"))
+    try:
+        err = nearest_error(12, 0, 10, 0.37 + 0.11j)
+    except ArpackNoConvergence:      # the far end of (A - sigma B)^{-1} B does not even converge
+        err = np.inf
+    assert err > 1e-3
+
+
+def test_radius_off_by_one_is_caught(monkeypatch):
+    def bad(distances, count):
+        d = np.sort(np.asarray(distances))
+        return 0.5 * (float(d[count]) + float(d[count + 1]))
+    monkeypatch.setattr(reference_eigs, "disk_radius", bad)
+    import test_oracle_reference_eigs as pins
+    with pytest.raises(AssertionError):
+        pins.test_disk_radius_hand_built_and_exact_count()
+
+
+def test_median_without_tie_break_is_caught(monkeypatch):
+    monkeypatch.setattr(reference_eigs, "median_eigenvalue",
+                        lambda lam: np.asarray(lam)[np.argsort(np.asarray(lam).real, kind="stable")][len(lam) // 2])
+    import test_oracle_reference_eigs as pins
+    with pytest.raises(AssertionError):
+        pins.test_median_eigenvalue_hand_built()
