@@ -78,7 +78,11 @@ typedef struct {
                              factors are kept in complex64 (rounded from the complex128
                              factorisation), the triangular solves run in FP32, and each
                              K_i^{-1} b is refined in FP64: x += K~_i^{-1} (b - K_i x) */
-  int32_t refine_steps;   /* FP64 refinement steps per solve when precision = 1 (default 2) */
+  int32_t refine_steps;   /* precision = 1: at most this many FP64 refinement steps per solve
+                             (default 8). The steps stop earlier once the measured correction
+                             shows the accuracy the call needs is reached (the FP64 floor for
+                             ie_apply_G and the first G(Y) of a filter; a relaxed accuracy in
+                             the later GMRES steps) or once corrections stop shrinking. */
   int32_t adjoint;        /* 1: also prepare the conjugate-transpose solves K_i^{-H} with the same
                              factors (ie_apply_GH, ie_solve_left): the adjoint pencil in DIA
                              form, a row-major copy of each U factor (q * n * 2*kl entries,
@@ -87,7 +91,7 @@ typedef struct {
 } ie_opts;
 
 /* Fills defaults: k=16, driver=1, m_max=100, max_outer=10, tau_g=1e-2, tau=1e-10,
- * gmres_tol=1e-12, sigma = center, seed = 0, precision = 0, refine_steps = 2, adjoint = 0. */
+ * gmres_tol=1e-12, sigma = center, seed = 0, precision = 0, refine_steps = 8, adjoint = 0. */
 void ie_opts_default(ie_opts* opts);
 
 /* Counters and timings of the last ie_solve / ie_filter_apply on a handle. */
@@ -114,6 +118,9 @@ typedef struct {
   int64_t adj_launches;    /* conjugate-transpose band-solve launches since create (either precision) */
   double t_adj_ms;         /* their summed device time */
   double adj_flops;        /* their algorithmic flops (same count per launch as the forward solve) */
+  int64_t refine_solves;   /* precision = 1: FP32 refinement solves (each: q poles x the block) since create */
+  double refine_last_corr; /* precision = 1: the last refinement step's largest relative correction
+                              max |dx|_inf / |x|_inf over poles and columns (an error estimate) */
 } ie_stats;
 
 /* ie_create: computes the inner poles/weights (Eq. pwtp, q points) and the outer

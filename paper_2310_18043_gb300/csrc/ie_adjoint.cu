@@ -178,7 +178,7 @@ struct AdjArgsT {
   int64_t ldr, rstride;
   CT* Y;              // phase-1 result (and, mode 0, the output), column c at Y + pole*ystride + c*ldy
   int64_t ldy, ystride;
-  cplx* X;            // output for mode 1 (X = x) and mode 2 (X += x)
+  cplx* X;            // output for mode 1 (X = x); mode 3 writes x in place into Y
   int64_t ldx, xstride;
   int* status;
 };
@@ -237,9 +237,8 @@ __global__ void __maxnreg__(REGS) band_solve_adj_kernel(AdjArgsT<CT> a) {
     }
     if (a.mode == 1) {
       Xo[(int64_t)(c0 + c) * a.ldx + r] = to_d(xv);
-    } else if (a.mode == 2) {
-      cplx* p = &Xo[(int64_t)(c0 + c) * a.ldx + r];
-      *p = cadd(*p, to_d(xv));
+    } else if (a.mode == 3) {
+      Yo[(int64_t)(c0 + c) * a.ldy + r] = xv;   // in place, as mode 0: row r is no longer read
     }
   };
 
@@ -581,7 +580,7 @@ cudaError_t launch_band_solve_adj32(int q, int64_t n, int kl, int64_t n_pad, con
   if (k <= 0) return cudaSuccess;
   AdjArgsT<float2> a{};
   a.n = n; a.n_pad = n_pad; a.kl = kl; a.kv = 2 * kl; a.klp = (int)ldl; a.kvp = 2 * kl;
-  a.k = k; a.mode = accumulate ? 2 : 1;
+  a.k = k; a.mode = accumulate ? 3 : 1;
   a.L = L32; a.ldl = ldl; a.lstride = n_pad * ldl;
   a.Ut = Ut32; a.ldu = 2 * kl; a.ustride = n_pad * 2 * kl;
   a.Ub = Ui32; a.Mb = M32; a.Hb = Hb; a.weights = d_wconj;

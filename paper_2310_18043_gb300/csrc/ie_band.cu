@@ -467,6 +467,46 @@ void launch_pole_residual(const DiaDev& P, const cplx* d_poles, int q, int k, co
   pole_residual_kernel<<<grid, 256, 0, s>>>(P, d_poles, BV, ldb, X, ldx, xstride, R32, ldr, rstride); ie_count_launch();
 }
 
+// Iterative-refinement update of the mixed-precision path: X[i][:, c] += D[i][:, c] (the FP32
+// correction K~_i^{-1} r, widened to FP64), and per (pole, column) the largest |.|_1 entry of
+// the correction and of the updated X, as float bits in nrm[(i*k + c)*2 + {0, 1}] (atomicMax on
+// non-negative floats; the caller zeroes nrm). Their ratio estimates the relative error that the
+// correction removed.
+__global__ void refine_add_kernel(int64_t n, int k, const float2* D, int64_t ldd, int64_t dstride,
+                                  cplx* X, int64_t ldx, int64_t xstride, unsigned* nrm) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int c = blockIdx.y, pole = blockIdx.z;
+  float md = 0.0f, mx = 0.0f;
+  if (i < n) {
+    const float2 d = D[(int64_t)pole * dstride + (int64_t)c * ldd + i];
+    cplx* xp = X + (int64_t)pole * xstride + (int64_t)c * ldx + i;
+    const cplx x = make_double2(xp->x + (double)d.x, xp->y + (double)d.y);
+    *xp = x;
+    md = fabsf(d.x) + fabsf(d.y);
+    mx = (float)cabs1(x);
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    md = fmaxf(md, __shfl_xor_sync(0xffffffffu, md, o));
+    mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  }
+  __shared__ float smd[8], smx[8];
+  if ((threadIdx.x & 31) == 0) { smd[threadIdx.x >> 5] = md; smx[threadIdx.x >> 5] = mx; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) { md = fmaxf(md, smd[w]); mx = fmaxf(mx, smx[w]); }
+    unsigned* o = nrm + ((int64_t)pole * k + c) * 2;
+    atomicMax(o, __float_as_uint(md));
+    atomicMax(o + 1, __float_as_uint(mx));
+  }
+}
+
+void launch_refine_add(int q, int64_t n, int k, const float2* D, int64_t ldd, int64_t dstride,
+                       cplx* X, int64_t ldx, int64_t xstride, unsigned* nrm, cudaStream_t s) {
+  if (k <= 0) return;
+  dim3 grid((unsigned)((n + 255) / 256), (unsigned)k, (unsigned)q);
+  refine_add_kernel<<<grid, 256, 0, s>>>(n, k, D, ldd, dstride, X, ldx, xstride, nrm); ie_count_launch();
+}
+
 __global__ void to_c64_kernel(int64_t n, const cplx* X, int64_t ldx, float2* Y, int64_t ldy) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int c = blockIdx.y;

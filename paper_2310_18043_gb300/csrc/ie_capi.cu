@@ -51,6 +51,10 @@ ie_status map_err(cudaError_t e) {
     if (s_ != IE_OK) return s_;    \
   } while (0)
 
+// Relative accuracy asked of a mixed-precision G-application outside the relaxed GMRES steps:
+// about 9 units of FP64 rounding, so refinement runs until it reaches the FP64 floor.
+constexpr double kRefineFull = 1e-15;
+
 struct ie_handle_s {
   int dev = 0;
   int64_t n = 0, n_pad = 0;
@@ -105,8 +109,16 @@ struct ie_handle_s {
   int* status = nullptr;
   int lu_ctas = 0;
   // mixed precision (opts.precision = 1): complex64 factors and FP32-solve scratch
-  int precision = 0, refine = 2, klp = 0;
-  int refine_cur = -1;     // refinement steps for the next G-application (-1: refine)
+  int precision = 0, refine = 8, klp = 0;
+  // Refinement control (see apply_G_mixed): the relative accuracy the next G-application
+  // needs (0: as accurate as FP64 refinement gets), the last measured relative error of the
+  // plain FP32 solve and the last measured contraction per refinement step (< 0: unknown).
+  double refine_target = 1e-15;
+  double ref_eps0 = -1.0, ref_c = -1.0;
+  unsigned* d_rnrm = nullptr;   // q * kmax * 2: correction / solution maxima (float bits)
+  std::vector<unsigned> h_rnrm;
+  int64_t refine_solves = 0;
+  double refine_last_corr = 0.0;
   float2* L32 = nullptr;   // q * n_pad * klp
   float2* U32 = nullptr;   // q * n_pad * kv
   float2* dinv32 = nullptr;
@@ -210,7 +222,7 @@ extern "C" void ie_opts_default(ie_opts* o) {
   o->sigma_is_center = 1;
   o->seed = 0;
   o->precision = 0;
-  o->refine_steps = 2;
+  o->refine_steps = 8;
   o->adjoint = 0;
 }
 
@@ -513,8 +525,10 @@ extern "C" ie_status ie_create(const ie_pencil* pen, ie_complex center, double r
         h->alloc(&h->dinv32, (size_t)q * h->n_pad) != cudaSuccess ||
         h->alloc(&h->Y32, (size_t)q * nk) != cudaSuccess ||
         h->alloc(&h->R32, (size_t)q * nk) != cudaSuccess ||
-        h->alloc(&h->BV32, nk) != cudaSuccess)
+        h->alloc(&h->BV32, nk) != cudaSuccess ||
+        h->alloc(&h->d_rnrm, (size_t)q * h->kmax * 2) != cudaSuccess)
       return fail(IE_ERR_OOM);
+    h->h_rnrm.assign((size_t)q * h->kmax * 2, 0u);
     launch_factors_to_c64(q, h->n_pad, kl, h->ldab, h->klp, h->AB, h->dinv, h->L32, h->U32,
                           h->dinv32, s);
     if (cudaStreamSynchronize(s) != cudaSuccess) return fail(IE_ERR_CUDA);
@@ -631,21 +645,28 @@ static ie_status apply_G_dev(ie_handle h, const cplx* V, int64_t ldv, const int6
 }
 
 // Mixed precision (opts.precision = 1), B V already in h->BVw: per pole i,
-//   x_i = K~_i^{-1} BV (complex64 factors, FP32 solve), then refine_steps times
-//   x_i += K~_i^{-1} (BV - K_i x_i) with the residual in FP64; GV = sum_i w_i x_i.
+//   x_i = K~_i^{-1} BV (complex64 factors, FP32 solve), then FP64 iterative refinement
+//   x_i += K~_i^{-1} (BV - K_i x_i), with the residual formed in FP64 from the DIA pencil;
+//   GV = sum_i w_i x_i in FP64.
 // The adjoint side uses K_i^H = conj(p_i) B^H - A^H and conj(w_i) throughout.
+//
+// The number of refinement steps is measured, not fixed. After step t the largest relative
+// correction d_t = max_{i,c} |dx_{i,c}|_inf / |x_{i,c}|_inf estimates the error that step
+// removed; refinement contracts the error by about c = d_t / d_{t-1} per step, so the error
+// left is about c d_t. The steps stop when that estimate is at most h->refine_target, when
+// the corrections stop shrinking (d_t > d_{t-1} / 2: the FP64 residual's own rounding floor),
+// or after opts.refine_steps steps. The GMRES loop passes larger targets as its residual falls
+// (relaxation, see filter_dev). When
+// the last application measured a plain-solve error eps0 with 10 eps0 <= target, no step is
+// taken. Outside the relaxed GMRES steps the target is kRefineFull.
 static ie_status apply_G_mixed(ie_handle h, int k, cplx* GV, int64_t ldg, cudaStream_t s) {
   const int64_t n = h->n, ps = n * (int64_t)h->kmax;
   const double nn = (double)n, kl = h->kl, kv = h->kv, q = h->q;
   const double fwd = nn * kl - 0.5 * kl * (kl + 1), bwd = nn * kv - 0.5 * kv * (kv + 1);
   const double flops = q * k * (8.0 * (fwd + bwd) + 12.0 * nn);
   const bool adj = h->side != 0;
-  launch_to_c64(n, k, h->BVw, n, h->BV32, n, s);
-  const int nref = h->refine_cur >= 0 ? std::min(h->refine_cur, h->refine) : h->refine;
-  for (int it = 0; it <= nref; ++it) {
-    if (it > 0)
-      launch_pole_residual(h->pen(), adj ? h->d_pconj : h->d_poles, h->q, k, h->BVw, n, h->Xp, n,
-                           ps, h->R32, n, ps, s);
+  const double target = h->refine_target;
+  auto solve = [&](int it) -> ie_status {
     ie_handle_s::SolveRec rec;
     rec.a = h->get_event();
     rec.b = h->get_event();
@@ -656,6 +677,7 @@ static ie_status apply_G_mixed(ie_handle h, int k, cplx* GV, int64_t ldg, cudaSt
     cudaEventRecord(rec.a, s);
     const float2* rhs = it == 0 ? h->BV32 : h->R32;
     const int64_t rstride = it == 0 ? 0 : ps;
+    // it = 0: X = K~^{-1} BV; it > 0: the correction K~^{-1} r in place into Y32
     if (adj) {
       CK(launch_band_solve_adj32(h->q, n, h->kl, h->n_pad, h->L32, h->klp, h->Ut32, h->Ub32,
                                  h->Madj32, h->Hb, h->d_wconj, rhs, n, rstride, k, h->Y32, n, ps,
@@ -667,25 +689,43 @@ static ie_status apply_G_mixed(ie_handle h, int k, cplx* GV, int64_t ldg, cudaSt
     }
     cudaEventRecord(rec.b, s);
     h->pending.push_back(rec);
+    return IE_OK;
+  };
+  launch_to_c64(n, k, h->BVw, n, h->BV32, n, s);
+  CKS(solve(0));
+  const bool skip = h->ref_eps0 > 0.0 && 10.0 * h->ref_eps0 <= target;
+  double prev = -1.0, last = 0.0;
+  const size_t nn2 = (size_t)h->q * k * 2;
+  for (int it = 1; it <= h->refine && !skip; ++it) {
+    launch_pole_residual(h->pen(), adj ? h->d_pconj : h->d_poles, h->q, k, h->BVw, n, h->Xp, n,
+                         ps, h->R32, n, ps, s);
+    CKS(solve(it));
+    CK(cudaMemsetAsync(h->d_rnrm, 0, sizeof(unsigned) * nn2, s));
+    launch_refine_add(h->q, n, k, h->Y32, n, ps, h->Xp, n, ps, h->d_rnrm, s);
+    CK(cudaMemcpyAsync(h->h_rnrm.data(), h->d_rnrm, sizeof(unsigned) * nn2, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    h->refine_solves += 1;
+    double d = 0.0;
+    for (size_t e = 0; e < nn2; e += 2) {
+      float dm, xm;
+      std::memcpy(&dm, &h->h_rnrm[e], sizeof(float));
+      std::memcpy(&xm, &h->h_rnrm[e + 1], sizeof(float));
+      if (xm > 0.0f) d = std::max(d, (double)dm / (double)xm);
+    }
+    last = d;
+    if (it == 1) h->ref_eps0 = d;
+    if (prev > 0.0) {
+      if (d > 0.5 * prev) break;                 // no longer shrinking: the FP64 floor
+      h->ref_c = std::min(1.0, d / prev);
+    }
+    const double c = prev > 0.0 ? d / prev : (h->ref_c > 0.0 ? 10.0 * h->ref_c : 1.0);
+    if (d * std::min(1.0, c) <= target) break;
+    prev = d;
   }
+  h->refine_last_corr = last;
   launch_pole_wsum(h->q, n, k, h->Xp, n, ps, adj ? h->d_wconj : h->d_weights, GV, ldg, s);
   h->g_columns += k;
   return IE_OK;
-}
-
-// Refinement steps for an Arnoldi step of the mixed-precision path, relaxed as GMRES converges
-// (inexact Krylov methods: Bouras & Fraysse, SIAM J. Matrix Anal. Appl. 26, 2005; Simoncini &
-// Szyld, SIAM J. Sci. Comput. 25, 2003): an operator error eps at a step whose residual is r
-// changes the final residual by about eps * r, so eps may grow as r falls. With s refinement
-// steps the relative error of K_i^{-1} b is taken as 1e-3, 1e-8, 1e-13 for s = 0, 1, 2 (ten
-// times the errors measured for complex64 factors), and the fewest steps with
-// eps_s * r <= tol / 50 are used (50: a bound on the number of steps that add such errors).
-static int relaxed_refine(const ie_handle h, double r) {
-  static const double eps[3] = {1e-3, 1e-8, 1e-13};
-  const double tol = h->opts.gmres_tol;
-  for (int s_ = 0; s_ < h->refine && s_ < 3; ++s_)
-    if (eps[s_] * r <= tol / 50.0) return s_;
-  return h->refine;
 }
 
 // ------------------------------ filter (multi-shift GMRES) -----------------------------------
@@ -753,9 +793,13 @@ static ie_status filter_dev(ie_handle h, const cplx* Y, int64_t ldy, int k, cplx
     const int kact = (int)act.size();
     CK(cudaMemcpyAsync(h->d_act, act.data(), sizeof(int) * kact, cudaMemcpyHostToDevice, s));
     launch_active_offsets(h->K, h->d_act, kact, h->d_off, s);
-    if (h->precision == 1) h->refine_cur = relaxed_refine(h, rmax);
+    // Inexact Krylov relaxation (Bouras & Fraysse, SIAM J. Matrix Anal. Appl. 26, 2005;
+    // Simoncini & Szyld, SIAM J. Sci. Comput. 25, 2003): an operator error eps at a step whose
+    // residual is r changes the final residual by about eps * r, so the mixed-precision path
+    // may refine G v_j only to tol / (50 r) (50: a bound on the steps that add such errors).
+    if (h->precision == 1) h->refine_target = std::min(1e-2, tol / (50.0 * rmax));
     const ie_status ga = apply_G_dev(h, h->K.V, n, h->d_off, kact, h->Wb, n, s);   // w = G v_j
-    h->refine_cur = -1;
+    h->refine_target = kRefineFull;
     CKS(ga);
     launch_arnoldi_cgs2(h->K, h->d_act, kact, h->Wb, n, h->hbuf, h->scratch, s);
     launch_givens(h->K, h->d_act, kact, h->d_shifts, nshift, h->rot_c, h->rot_s, h->gvec, 0,
@@ -1302,6 +1346,8 @@ static void fill_solve_stats(ie_handle h, ie_stats* out) {
   out->adj_launches = h->adj_launches;
   out->t_adj_ms = h->t_adj_ms;
   out->adj_flops = h->adj_flops;
+  out->refine_solves = h->refine_solves;
+  out->refine_last_corr = h->refine_last_corr;
 }
 
 extern "C" ie_status ie_get_stats(ie_handle h, ie_stats* out) {

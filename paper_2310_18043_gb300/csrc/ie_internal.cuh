@@ -124,7 +124,8 @@ cudaError_t launch_band_solve(int q, int64_t n, int kl, int64_t n_pad, const cpl
 void launch_block_transforms(int q, int64_t n, int64_t n_pad, int kl, int ldab, const cplx* AB,
                              const int* piv, const cplx* dinv, cplx* T, int* H, cplx* Ui,
                              float2* T32, float2* Ui32, cudaStream_t s);
-// Mixed precision: complex64 band solves; X (FP64, per pole) = x (accumulate = 0) or += x.
+// Mixed precision: complex64 band solves; X (FP64, per pole) = x (accumulate = 0), or
+// (accumulate = 1) x is written in place over the forward result in Y32 and X is untouched.
 // RHS column c of pole i at RHS + i*rstride + c*ldr (rstride 0: shared right-hand side).
 cudaError_t launch_band_solve32(int q, int64_t n, int kl, int64_t n_pad, const float2* L32,
                                 int64_t ldl, const float2* U32, int64_t ldu, const int* piv,
@@ -144,6 +145,11 @@ void launch_pole_residual(const DiaDev& P, const cplx* d_poles, int q, int k, co
                           int64_t ldr, int64_t rstride, cudaStream_t s);
 void launch_to_c64(int64_t n, int k, const cplx* X, int64_t ldx, float2* Y, int64_t ldy,
                    cudaStream_t s);
+// X[i] += D[i] (FP32 correction widened to FP64) for all q poles; per (pole, column) the
+// largest |.|_1 of the correction and of the new X into nrm[(i*k + c)*2 + {0,1}] as float bits
+// (atomicMax; zero nrm first).
+void launch_refine_add(int q, int64_t n, int k, const float2* D, int64_t ldd, int64_t dstride,
+                       cplx* X, int64_t ldx, int64_t xstride, unsigned* nrm, cudaStream_t s);
 // GV[:, c] = sum_i w_i Xp[i][:, c]
 void launch_pole_wsum(int q, int64_t n, int k, const cplx* Xp, int64_t ldx, int64_t xstride,
                       const cplx* w, cplx* GV, int64_t ldg, cudaStream_t s);
@@ -234,7 +240,8 @@ cudaError_t launch_band_solve_adj(int q, int64_t n, int kl, int64_t n_pad, const
                                   const cplx* d_wconj, const cplx* RHS, int64_t ldr, int k,
                                   cplx* Xp, int64_t ldx, int64_t xstride, int* status,
                                   cudaStream_t s);
-// complex64 factors, FP32 solve: X (FP64, per pole) = K~_i^{-H} RHS_i (accumulate = 0) or +=.
+// complex64 factors, FP32 solve: X (FP64, per pole) = K~_i^{-H} RHS_i (accumulate = 0), or
+// (accumulate = 1) the solution in place into Y32 (complex64), X untouched.
 cudaError_t launch_band_solve_adj32(int q, int64_t n, int kl, int64_t n_pad, const float2* L32,
                                     int64_t ldl, const float2* Ut32, const float2* Ui32,
                                     const float2* M32, const int* Hb, const cplx* d_wconj,

@@ -52,7 +52,8 @@ struct SolveArgsT {
   int64_t ldr, rstride;
   CT* Y;              // forward result, column c at Y + pole*ystride + c*ldy
   int64_t ldy, ystride;
-  cplx* X;            // output (mode 0: X == Y, X = w*x; mode 1: X = x; mode 2: X += x)
+  cplx* X;            // output (mode 0: X == Y, X = w*x; mode 1: X = x; mode 3: x written in
+                      // place into Y in the element type, X untouched)
   int64_t ldx, xstride;
   int* status;
 };
@@ -261,9 +262,6 @@ __global__ void __maxnreg__(REGS) band_solve_kernel(SolveArgsT<CT> a) {
   };
   const int Sb = kv + NB;
   int64_t row[SPT];
-  // mode 2 (complex64 path only): the FP64 value the row's result is added to, loaded on entry
-  constexpr bool kAcc = sizeof(CT) == sizeof(float2);
-  cplx xold[kAcc ? SPT : 1][kAcc ? NC : 1];
   if (tid == 0)
     for (int st = 0; st < a.nstage && st < npanel; ++st) issue_bwd(st, st);
   {
@@ -279,12 +277,6 @@ __global__ void __maxnreg__(REGS) band_solve_kernel(SolveArgsT<CT> a) {
         const int64_t rn = r - Sb;
         nxt[u][c] = (s < Sb && rn >= 0 && rn < n && c < ncol) ? Yo[(int64_t)(c0 + c) * a.ldy + rn]
                                                              : zero;
-      }
-      if constexpr (kAcc) {
-#pragma unroll
-        for (int c = 0; c < NC; ++c)
-          xold[u][c] = (a.mode == 2 && s < Sb && r >= 0 && r < n && c < ncol)
-                           ? Xo[(int64_t)(c0 + c) * a.ldx + r] : make_double2(0, 0);
       }
       if (s < Sb && r > j0 - NB)
 #pragma unroll
@@ -333,8 +325,8 @@ __global__ void __maxnreg__(REGS) band_solve_kernel(SolveArgsT<CT> a) {
             }
             if (a.mode == 1) {
               Xo[(int64_t)(c0 + c) * a.ldx + r] = to_d(xv);
-            } else if constexpr (kAcc) {
-              Xo[(int64_t)(c0 + c) * a.ldx + r] = cadd(xold[u][c], to_d(xv));
+            } else if (a.mode == 3) {
+              Yo[(int64_t)(c0 + c) * a.ldy + r] = xv;   // row r of y is no longer read
             }
           }
         }
@@ -345,9 +337,6 @@ __global__ void __maxnreg__(REGS) band_solve_kernel(SolveArgsT<CT> a) {
           v[u][c] = nxt[u][c];
           const int64_t rn = r - Sb;
           nxt[u][c] = (rn >= 0 && c < ncol) ? Yo[(int64_t)(c0 + c) * a.ldy + rn] : zero;
-          if constexpr (kAcc)
-            xold[u][c] = (a.mode == 2 && r >= 0 && c < ncol) ? Xo[(int64_t)(c0 + c) * a.ldx + r]
-                                                             : make_double2(0, 0);
         }
         // a refilled row lies below every column of this block's band: no update; with
         // kv < NB it can already be a head row of the next block
@@ -692,7 +681,7 @@ cudaError_t launch_band_solve32(int q, int64_t n, int kl, int64_t n_pad, const f
   SolveArgsT<float2> a{};
   a.n = n; a.n_pad = n_pad; a.kl = kl; a.kv = 2 * kl;
   a.klp = (int)ldl; a.kvp = (int)ldu;   // padded column lengths = column strides
-  a.k = k; a.mode = accumulate ? 2 : 1;
+  a.k = k; a.mode = accumulate ? 3 : 1;
   a.L = L32; a.U = U32; a.ldl = ldl; a.ldu = ldu;
   a.lstride = n_pad * ldl; a.ustride = n_pad * ldu;
   a.piv = piv; a.dinv = dinv32; a.weights = d_weights;

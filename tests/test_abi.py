@@ -101,7 +101,7 @@ def test_status_strings_and_defaults(lib):
     o = ie.ie_opts_default()
     assert (o.k, o.driver, o.m_max, o.max_outer) == (16, 1, 100, 10)
     assert (o.tau_g, o.tau, o.gmres_tol, o.sigma_is_center) == (1e-2, 1e-10, 1e-12, 1)
-    assert (o.precision, o.refine_steps, o.adjoint) == (0, 2, 0)
+    assert (o.precision, o.refine_steps, o.adjoint) == (0, 8, 0)
 
 
 def test_argument_checks_need_no_gpu(lib):

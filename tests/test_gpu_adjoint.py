@@ -13,7 +13,7 @@ import scipy.linalg as sla
 import ie_inputs
 from oracle import adjoint as oadj, pencil as opencil
 
-from test_gpu_parity import Case, dblock, dzeros
+from test_gpu_parity import colerr, Case, dblock, dzeros
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -41,6 +41,7 @@ def test_apply_GH_matches_oracle(ie, name, k):
         ref = oadj.adjoint_inner(c.A, c.B, c.w["center"], c.w["radius"], c.w["q"]).apply(V)
         err = np.linalg.norm(GVd.cpu().numpy() - ref, axis=0) / np.linalg.norm(ref, axis=0)
         assert err.max() < 1e-11, err.max()
+        assert colerr(GVd.cpu().numpy(), ref).max() < 1e-11
         _, st = ie.ie_get_stats(c.h)
         assert st["adj_launches"] == 1
     finally:
@@ -78,8 +79,10 @@ def test_apply_GH_mixed_precision(ie):
         ref = oadj.adjoint_inner(c.A, c.B, c.w["center"], c.w["radius"], c.w["q"]).apply(V)
         err = np.linalg.norm(GVd.cpu().numpy() - ref, axis=0) / np.linalg.norm(ref, axis=0)
         assert err.max() < 1e-11, err.max()
+        assert colerr(GVd.cpu().numpy(), ref).max() < 1e-11
         _, st = ie.ie_get_stats(c.h)
-        assert st["adj_launches"] == 1 + 2 and st["solve_launches"] == 0
+        assert st["refine_solves"] >= 1
+        assert st["adj_launches"] == 1 + st["refine_solves"] and st["solve_launches"] == 0
     finally:
         c.close()
 

@@ -8,7 +8,7 @@ import pytest
 import ie_inputs
 from oracle import inner, msgmres, hsrr as ohsrr
 
-from test_gpu_parity import Case, dblock, dzeros, golden_eigs, match_eigs
+from test_gpu_parity import Case, colerr, dblock, dzeros, golden_eigs, match_eigs
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -37,28 +37,33 @@ def oracle_G(c2):
 
 
 def test_c2_apply_G_sampled_columns(ie, c2, oracle_G):
-    """Full 64-column launch; the oracle checks 3 sampled columns (first, middle, last)."""
+    """Full 64-column launch; the oracle checks 5 sampled columns (first, the edges of a
+    column group, middle, last), element by element."""
     k = 64
     V = ie_inputs.random_block(c2.n, k, seed=21)
     GVd = dzeros(c2.n, k)
     assert ie.ie_apply_G(c2.h, dblock(V), GVd) == ie.IE_OK
     got = GVd.cpu().numpy()
-    for col in (0, 31, 63):
-        ref = oracle_G.apply(V[:, col])
-        err = np.linalg.norm(got[:, col] - ref) / np.linalg.norm(ref)
-        assert err < 1e-11, (col, err)
+    cols = [0, 3, 4, 31, 63]
+    ref = oracle_G.apply(V[:, cols])
+    err = colerr(got[:, cols], ref)
+    assert err.max() < 1e-11, dict(zip(cols, err))
+    nerr = np.linalg.norm(got[:, cols] - ref, axis=0) / np.linalg.norm(ref, axis=0)
+    assert nerr.max() < 1e-11
 
 
-def test_c2_filter_sampled_column(ie, c2, oracle_G):
-    """Filter of the full bench block; the oracle filters one sampled column."""
+def test_c2_filter_sampled_columns(ie, c2, oracle_G):
+    """Filter of the full bench block; the oracle filters 4 sampled columns (first, two
+    inside, last), compared element by element."""
     k = 64
     Y = ie_inputs.orthonormal_random_block(c2.n, k, seed=1)
     Ud = dzeros(c2.n, k)
     assert ie.ie_filter_apply(c2.h, dblock(Y), Ud) == ie.IE_OK
     got = Ud.cpu().numpy()
-    ref = msgmres.filter_apply(oracle_G, Y[:, 17:18], c2.w["p"], tol=1e-12, m_max=150)
-    err = np.linalg.norm(got[:, 17] - ref[:, 0]) / np.linalg.norm(ref[:, 0])
-    assert err < 1e-9, err
+    cols = [0, 17, 40, 63]
+    ref = msgmres.filter_apply(oracle_G, Y[:, cols], c2.w["p"], tol=1e-12, m_max=150)
+    err = colerr(got[:, cols], ref)
+    assert err.max() < 1e-9, dict(zip(cols, err))
 
 
 @pytest.mark.parametrize("driver", [1, 2])
@@ -84,24 +89,25 @@ def test_c2_solve_matches_reference_eigenvalues(ie, driver):
         c.close()
 
 
-# Eigenvector condition allowance for the eigenvalue bound below. The convection-diffusion
-# part of A is similar to a symmetric matrix through the diagonal scaling exp(b.x/2) with
-# b = (3, 2); for modes spread over the unit square this gives
+# Eigenvector condition allowance for the extra first-order check below. The
+# convection-diffusion part of A is similar to a symmetric matrix through the diagonal
+# scaling exp(b.x/2) with b = (3, 2); for modes spread over the unit square this gives
 # ||x|| ||y|| / |y^H x| ~ sqrt(mean exp(b.x) * mean exp(-b.x)) = 1.67. The allowance 4 covers
 # B != I, the random imaginary diagonal and mode localisation.
 KAPPA_ALLOWANCE = 4.0
+C4_TAU = 1e-12
 
 
 def test_c4_mixed_precision_solve(ie):
     """The precision configuration: m = 512 (n = 262,144, band 512), q = p = 8, k = 96,
-    complex64 factors and FP32 band solves with FP64 refinement, Alg. 2, stop at rho < 1e-10.
-    All 60 reference eigenvalues (shift-invert Arnoldi) are found, every returned pair has
-    rho <= 1e-10, and each eigenvalue's error obeys the first-order perturbation bound of
-    its own backward error: |dl| / |l| <= kappa * rho * (||A||_1 + |l| ||B||_1) / |l|. A flat
-    1e-10 relative bar is not implied by rho <= 1e-10 here: the norm factor alone is about 3
-    at this size (||A||_1 ~ 8/h^2 against |l| ~ 4/h^2)."""
+    complex64 factors and FP32 band solves with measured FP64 refinement, Alg. 2.
+    All 60 reference eigenvalues (shift-invert Arnoldi) are found, each to 1e-10 relative,
+    and every returned pair has rho <= 1e-10. The stop tolerance is tau = 1e-12: rho <= 1e-10
+    alone bounds the eigenvalue error only by about kappa * rho * (||A||_1 + |l| ||B||_1) / |l|,
+    a norm factor near 3 at this size. As an extra check each error also obeys that
+    first-order bound of its own rho."""
     from oracle import pencil as opencil
-    c = Case(ie, "c4_m512", driver=2, m_max=150, precision=1)
+    c = Case(ie, "c4_m512", driver=2, m_max=150, precision=1, tau=C4_TAU)
     try:
         k = c.w["k"]
         Y0 = ie_inputs.orthonormal_random_block(c.n, k, seed=c.w["seed"])
@@ -112,14 +118,15 @@ def test_c4_mixed_precision_solve(ie):
         assert nf == len(ref) == 60
         lam, rho = np.asarray(lam[:nf]), np.asarray(rho[:nf])
         assert np.all(rho <= 1e-10), rho.max()
+        err = match_eigs(lam, ref, rel=1e-10)
+        print(f"c4 mixed: max eigenvalue rel err {err:.2e}, max rho {rho.max():.2e}, "
+              f"refinement solves {stats['refine_solves']}")
         d = np.abs(lam[:, None] - ref[None, :])
         j = np.argmin(d, axis=1)
-        assert sorted(j) == list(range(len(ref))), "not a one-to-one match"
-        err = np.min(d, axis=1) / np.abs(ref[j])
+        errs = np.min(d, axis=1) / np.abs(ref[j])
         scale = (opencil.norm1(c.A) + np.abs(lam) * opencil.norm1(c.B)) / np.abs(lam)
         bound = KAPPA_ALLOWANCE * rho * scale + 1e-13
-        worst = int(np.argmax(err / bound))
-        assert np.all(err <= bound), (err[worst], rho[worst], scale[worst])
+        assert np.all(errs <= bound), (errs.max(), rho.max())
         assert stats["solve32_launches"] > 0 and stats["solve_launches"] == 0
     finally:
         c.close()
