@@ -30,6 +30,9 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 WORKLOAD = "c2_m256"
+METRIC = "filtered columns/sec"
+MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
+HBM_FALLBACK_GBS = 6800.0
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12     # 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # 152 SMs x 128 FP32 FMA/clk x 2 flop x 2.07 GHz
 # DRAM traffic of one complex128 band_solve_kernel launch per algorithmic byte, from the ncu
@@ -65,10 +68,30 @@ def parse():
                     help="1: also time left eigenvectors + eigenvalue sensitivities (adjoint "
                          "pencil) and the conjugate-transpose band-solve kernel; 2: only that "
                          "kernel")
+    ap.add_argument("--c4", type=int, default=1,
+                    help="1: also time the precision workload c4_m512 (n = 262,144, band 512, "
+                         "k = 96): mixed precision, Alg. 2, tau = 1e-12, time to all eigenpairs "
+                         "in D and the error against the FP64 reference eigenvalues")
     ap.add_argument("--precision", type=int, default=0, choices=[0, 1],
                     help="0: complex128 factors and solves; 1: complex64 factors, FP32 solves, "
                          "FP64 refinement")
     return ap.parse_args()
+
+
+def hbm_peak():
+    """(GB/s, source): the measured copy bandwidth of the GB300s, else the fallback."""
+    try:
+        with open(MEASURED_PEAKS) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return HBM_FALLBACK_GBS, "fallback"
+
+
+def r3(x):
+    """Three significant digits (keeps the printed line short)."""
+    if x is None or isinstance(x, (bool, str)):
+        return x
+    return float(f"{x:.3g}")
 
 
 # ------------------------------------------------------------------ distributed plumbing
@@ -271,7 +294,8 @@ def run_native(args):
                 "n_in_disk_reference": int(len(ref)), "max_rho": float(np.max(rho[:nf])) if nf else None,
                 "max_rel_err_vs_reference": err, "outer_iters": sst["outer_iters"],
                 "p_final": sst["p_final"], "factor_ms": sst["t_factor_ms"],
-                "filter_ms": sst["t_filter_ms"], "hsrr_ms": sst["t_hsrr_ms"]}
+                "filter_ms": sst["t_filter_ms"], "hsrr_ms": sst["t_hsrr_ms"],
+                "refine_solves": sst["refine_solves"]}
             ie.ie_destroy(hs)
         return out
 
@@ -324,7 +348,7 @@ def run_native(args):
         mms = mB["t_solve32_ms"] - mA["t_solve32_ms"]
         mfl = mB["solve32_flops"] - mA["solve32_flops"]
         ie.ie_destroy(h)
-        mixed = {"dtype": "c64 factors and solves, f64 refinement (2 steps), f64 Krylov/HSRR",
+        mixed = {"dtype": "c64 factors and solves, measured f64 refinement, f64 Krylov/HSRR",
                  "value": k * args.steps / (tm / 1e3), "unit": "filtered columns/s",
                  "ms_per_step": tm / args.steps,
                  "ritz_in_disk_rho_max": float(np.max(last["rho"][ins])) if ins.any() else None,
@@ -348,59 +372,170 @@ def run_native(args):
         sens = time_sensitivities(ie, w, pen, A_d, B_d, device, stream, Xd,
                                   kernel_only=args.sens == 2)
 
+    c4 = None
+    if args.c4 and rank == 0:
+        c4 = time_c4(ie, device, stream)
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         cpu = cpu_baseline(args.workload)
-        cpu["all_cores"] = cpu_baseline_all_cores(args.workload)
+        allc = cpu_baseline_all_cores(args.workload)
+        cpu.update({"all_cores_value": allc["value"], "all_cores_procs": allc["cores"],
+                    "host_cores": allc["host_cores"], "all_cores_sample": allc["sample"]})
 
     if rank == 0:
         inside = np.abs(last["lam"] - w["center"]) < w["radius"]
         achieved = solve_fl / (solve_ms / 1e3) / 1e12 if solve_ms > 0 else None
         peak = FP64_PEAK_TFLOPS if args.precision == 0 else FP32_PEAK_TFLOPS
+        hbm, hbm_src = hbm_peak()
+        alg_bytes = solve_by / launches if (launches and solve_by) else None
+        avg_ms = solve_ms / launches if launches else None
+        hbm_gbs = alg_bytes / (avg_ms / 1e3) / 1e9 if (alg_bytes and avg_ms) else None
+        roofline = {
+            "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": achieved / peak if achieved else None,
+            "traffic": (C128_SOLVE_TRAFFIC_RATIO * alg_bytes
+                        if (args.precision == 0 and alg_bytes) else None),
+            "kernel": "band_solve_kernel (%s complex band solves)"
+                      % ("FP64" if args.precision == 0 else "FP32"),
+            "peak_source": ("derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz "
+                            "(measured FP64 FMA probe: 1.20 TFLOP/s)")
+                           if args.precision == 0 else
+                           ("derived: 152 SMs x 128 FP32 FMA/clk x 2 flop x 2.07 GHz "
+                            "(measured FP32 FMA probe: 70.2 TFLOP/s)"),
+            "traffic_source": ("ncu capture at p1_m160 scaled by algorithmic bytes"
+                               if args.precision == 0 else None),
+            "algorithmic_bytes_per_launch": alg_bytes,
+            "algorithmic_flops_per_launch": solve_fl / launches if launches else None,
+            "launches": launches, "avg_launch_ms": avg_ms,
+            "share_of_step": solve_ms / t_ms if t_ms > 0 else None,
+            # the HBM roof of the same kernel (its algorithmic bytes / launch time): far below
+            # 1 because the FP64 (or FP32) arithmetic per byte binds first
+            "hbm_achieved_gbs": hbm_gbs, "hbm_peak_gbs": hbm,
+            "hbm_frac": hbm_gbs / hbm if hbm_gbs else None,
+            "hbm_peak_source": hbm_src + " (MEASURED_PEAKS.json hbm_gbs)"
+                               if hbm_src == "measured" else "fallback 6.8 TB/s"}
+        details = {"factor_ms": s0["t_factor_ms"], "create_s": create_s,
+                   "gmres_iters_max": last["gmres"], "ritz_in_disk": int(inside.sum()),
+                   "ritz_in_disk_rho_max": (float(np.max(last["rho"][inside]))
+                                            if inside.any() else None),
+                   "time_to_all_eigenpairs": solves, "mixed_precision": mixed,
+                   "sensitivities": sens, "batch": batch, "simple_rule": simple, "c4": c4}
         line = {
-            "metric": "filtered columns/sec (one Alg. 1 outer iteration: composite filter + HSRR)",
+            "metric": METRIC,
             "value": value, "unit": "filtered columns/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
             "dtype": "c128" if args.precision == 0 else "c64 solves + f64 refinement",
             "data": "synthetic",
+            "step": "one Alg. 1 outer iteration on the k-column block: composite filter + HSRR",
             "config": workload_config(args.workload, world),
-            "details": {"factor_ms": s0["t_factor_ms"], "create_s": create_s,
-                        "gmres_iters_max": last["gmres"],
-                        "ritz_in_disk": int(inside.sum()),
-                        "ritz_in_disk_rho_max": (float(np.max(last["rho"][inside]))
-                                                 if inside.any() else None)},
-            "roofline": {"bound": "alu",
-                         "kernel": "band_solve_kernel (%s complex band solves)"
-                                   % ("FP64" if args.precision == 0 else "FP32"),
-                         "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                         "frac": achieved / peak if achieved else None,
-                         "peak_source": ("derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz "
-                                         "(measured FP64 FMA probe: 1.20 TFLOP/s)")
-                                        if args.precision == 0 else
-                                        ("derived: 152 SMs x 128 FP32 FMA/clk x 2 flop x 2.07 GHz "
-                                         "(measured FP32 FMA probe: 70.2 TFLOP/s)"),
-                         "traffic": (C128_SOLVE_TRAFFIC_RATIO * solve_by / launches
-                                     if (args.precision == 0 and launches and solve_by) else None),
-                         "traffic_source": ("ncu capture at p1_m160 scaled by algorithmic bytes"
-                                            if args.precision == 0 else None),
-                         "algorithmic_bytes_per_launch": solve_by / launches if (launches and solve_by) else None,
-                         "algorithmic_flops_per_launch": solve_fl / launches if launches else None,
-                         "launches": launches, "avg_launch_ms": solve_ms / launches if launches else None,
-                         "share_of_step": solve_ms / t_ms if t_ms > 0 else None},
+            "roofline": roofline,
             "gpu_launches": gpu_launches,
-            "time_to_all_eigenpairs": solves,
-            "mixed_precision": mixed,
-            "sensitivities": sens,
-            "batch": batch,
-            "simple_rule": simple,
             "e2e": e2e,
             "clocks": clk.summary(),
             "cpu_baseline": cpu,
+            "details": details,
+            # last, so that a reader of the printed line's final 1500 characters sees it whole
+            "results": compact_results(solves, mixed, c4, batch, simple, sens, roofline, cpu),
         }
         print(json.dumps(line))
     if dist is not None:
         dist.destroy_process_group()
+
+
+def compact_results(solves, mixed, c4, batch, simple, sens, roofline, cpu):
+    """Flat, rounded summary of the whole measurement (time to all eigenpairs per driver and
+    precision with their errors, the mixed-precision throughput, C4, batch, simple rule,
+    adjoint solve, HBM fraction). Keys: tta = time to all eigenpairs in D (s, create + solve),
+    err = max relative eigenvalue error against the reference eigenvalues, rho = max
+    residual of the returned pairs, nf = pairs found / reference count."""
+    out = {}
+
+    def tta(tag, d):
+        if not d:
+            return
+        for drv in ("alg1", "alg2"):
+            x = d.get(drv)
+            if not x:
+                continue
+            out[f"tta_{drv}_{tag}_s"] = r3(x["seconds"])
+            out[f"err_{drv}_{tag}"] = r3(x["max_rel_err_vs_reference"])
+            out[f"rho_{drv}_{tag}"] = r3(x["max_rho"])
+            out[f"nf_{drv}_{tag}"] = f'{x["n_found"]}/{x["n_in_disk_reference"]}'
+    tta("c128", solves)
+    if mixed:
+        tta("mixed", mixed.get("time_to_all_eigenpairs"))
+        out["mixed_cols_per_s"] = r3(mixed["value"])
+        b = mixed.get("band_solve_c64") or {}
+        if b.get("achieved_tflops"):
+            out["mixed_solve_ms"] = r3(b["avg_launch_ms"])
+            out["mixed_solve_frac_fp32"] = r3(b["achieved_tflops"] / b["peak_tflops"])
+    if c4:
+        for key in ("create_s", "lu_ms", "tta_s", "max_rel_err_vs_reference", "max_rho",
+                    "refine_solves"):
+            if key in c4:
+                out[f"c4_{key}"] = r3(c4[key])
+        if "n_found" in c4:
+            out["c4_nf"] = f'{c4["n_found"]}/{c4["n_in_disk_reference"]}'
+    if simple and "seconds" in simple:
+        out["simple_rule_tta_s"] = r3(simple["seconds"])
+    if batch and "speedup" in batch:
+        out["batch_speedup_c128"] = r3(batch["speedup"])
+        bm = batch.get("mixed_precision") or {}
+        if "speedup" in bm:
+            out["batch_speedup_mixed"] = r3(bm["speedup"])
+    if sens and (sens.get("band_solve_adj_c128") or {}).get("frac"):
+        out["adj_solve_frac_fp64"] = r3(sens["band_solve_adj_c128"]["frac"])
+    out["solve_frac_fp64"] = r3(roofline.get("frac"))
+    out["solve_hbm_frac"] = r3(roofline.get("hbm_frac"))
+    if cpu and cpu.get("all_cores_value"):
+        out["oracle_all_cores_cols_per_s"] = r3(cpu["all_cores_value"])
+    return out
+
+
+def time_c4(ie, device, stream):
+    """The precision workload c4_m512 (n = 262,144, band 512, q = p = 8, k = 96): complex64
+    factors, FP32 band solves with measured FP64 refinement, Alg. 2, stop at rho < 1e-12.
+    Time to all eigenpairs in D (ie_create + ie_solve) and the error of every eigenvalue
+    against the FP64 reference eigenvalues (oracle shift-invert Arnoldi, tests/golden)."""
+    import torch
+
+    import ie_inputs
+    w = ie_inputs.load_workload("c4_m512")
+    pen = ie_inputs.make_pencil(w["m"], w["seed"])
+    n, k = pen.n, w["k"]
+    A_d = torch.from_numpy(pen.A_dia).to(device)
+    B_d = torch.from_numpy(pen.B_dia).to(device)
+    o = ie.ie_opts_default(k=k, m_max=150, precision=1, driver=2, tau=1e-12)
+    Y0 = ie_inputs.orthonormal_random_block(n, k, seed=w["seed"])
+    Y0d = torch.from_numpy(np.ascontiguousarray(Y0.T)).to(device).T
+    X = torch.zeros((k, n), dtype=torch.complex128, device=device).T
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    st, h = ie.ie_create(n, pen.offsets, A_d, B_d, w["center"], w["radius"], w["p"], w["q"], o,
+                         stream)
+    torch.cuda.synchronize()
+    t_create = time.perf_counter() - t0
+    if st != ie.IE_OK:
+        return {"error": ie.ie_status_str(st)}
+    t0 = time.perf_counter()
+    st1, lam, rho, e, nf, sst = ie.ie_solve(h, Y0d, X, k, stream)
+    torch.cuda.synchronize()
+    t_solve = time.perf_counter() - t0
+    ie.ie_destroy(h)
+    ref = np.array(w["eig_in_disk_re"]) + 1j * np.array(w["eig_in_disk_im"])
+    got = lam[:nf]
+    err = (float(np.max(np.min(np.abs(got[:, None] - ref[None, :]), axis=1) / np.abs(got)))
+           if nf else None)
+    return {"workload": "c4_m512", "driver": 2, "tau": 1e-12, "status": ie.ie_status_str(st1),
+            "create_s": t_create, "lu_ms": sst["t_factor_ms"], "solve_s": t_solve,
+            "tta_s": t_create + t_solve, "n_found": nf, "n_in_disk_reference": int(len(ref)),
+            "max_rho": float(np.max(rho[:nf])) if nf else None,
+            "max_rel_err_vs_reference": err, "outer_iters": sst["outer_iters"],
+            "p_final": sst["p_final"], "refine_solves": sst["refine_solves"],
+            "solve32_launches": sst["solve32_launches"],
+            "t_solve32_ms": sst["t_solve32_ms"]}
 
 
 def time_simple_rule(ie, w, pen, A_d, B_d, device, stream, Xd, precision):
@@ -630,10 +765,12 @@ print(json.dumps({{"t_filter": tt, "t_factor": tf, "iters": st["gmres_iters"]}})
 """
 
 
-def cpu_baseline_all_cores(name, max_procs=16):
-    """The same oracle sample on every host core: one single-threaded process per core, each
-    factorising and filtering a different column of the block at the same time. Throughput =
-    processes / the slowest process's filter time (factorisations excluded)."""
+def cpu_baseline_all_cores(name, max_procs=72):
+    """The same oracle sample on every host core: one single-threaded process per core
+    (os.sched_getaffinity; at most max_procs, which bounds the host memory of the
+    factorisations, about 1 GB per process at m = 256), each factorising and filtering a
+    different column of the block at the same time. Throughput = processes / the slowest
+    process's filter time (factorisations excluded)."""
     try:
         cores = len(os.sched_getaffinity(0))
     except AttributeError:
@@ -645,10 +782,11 @@ def cpu_baseline_all_cores(name, max_procs=16):
           for i in range(procs)]
     outs = [p.communicate() for p in ps]
     if any(p.returncode != 0 for p in ps):
-        return {"value": None, "cores": procs, "sample": "failed"}
+        return {"value": None, "cores": procs, "host_cores": cores, "sample": "failed"}
     ds = [json.loads(o[0].strip().splitlines()[-1]) for o in outs]
     tmax = max(d["t_filter"] for d in ds)
-    return {"value": procs / tmax, "unit": "filtered columns/s", "cores": procs, "kind": "oracle",
+    return {"value": procs / tmax, "unit": "filtered columns/s", "cores": procs,
+            "host_cores": cores, "kind": "oracle",
             "sample": f"{procs} processes (one BLAS thread each), each the composite filter of "
                       f"one column of the same workload; factorisations excluded"}
 
@@ -685,8 +823,9 @@ def run_reference(args):
         vals.append(cb["value"])
     wall = time.perf_counter() - t0
     v = float(np.mean([x for x in vals if x])) if any(vals) else None
-    line = {"impl": "reference", "metric": "filtered columns/sec (one Alg. 1 outer iteration: "
-                                           "composite filter + HSRR)",
+    line = {"impl": "reference", "metric": METRIC,
+            "step": "the oracle's composite filter of one column of the block (HSRR, about 2% "
+                    "of a GPU step, is not in the sample)",
             "value": v, "unit": "filtered columns/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": wall * 1e3 / max(args.steps, 1),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128",
