@@ -74,9 +74,9 @@ typedef struct {
   int32_t sigma_is_center;/* 1: HSRR shift sigma = center (Sec. 6 preamble); 0: use sigma_re/im */
   double sigma_re, sigma_im;
   uint64_t seed;          /* seeds rank-guard replacement vectors and the random Y0 */
-  int32_t precision;      /* 0: complex128 band LU and solves. 1: mixed precision -- the
-                             factors are kept in complex64 (rounded from the complex128
-                             factorisation), the triangular solves run in FP32, and each
+  int32_t precision;      /* 0: complex128 band LU and solves. 1: mixed precision -- K_i is
+                             assembled in complex64 and factored by the band LU in FP32
+                             arithmetic, the triangular solves run in FP32, and each
                              K_i^{-1} b is refined in FP64: x += K~_i^{-1} (b - K_i x) */
   int32_t refine_steps;   /* precision = 1: at most this many FP64 refinement steps per solve
                              (default 8). The steps stop earlier once the measured correction
@@ -190,12 +190,12 @@ ie_status ie_get_coeffs(ie_handle h, ie_complex* h_poles, ie_complex* h_weights,
                         ie_complex* h_shifts, ie_complex* h_cweights, int32_t* n_shift,
                         double* odd_coef);
 
-/* ie_get_factor (complex128 handles only; IE_ERR_ARG for precision = 1, whose
- * complex128 factors are released after their complex64 copy is made):
- * copies pole i's band LU (LAPACK zgbtrf layout: column j holds
- * rows j-kv..j+kl at offsets 0..ldab-1 with kv = 2*kl, ldab = 3*kl + 1; U in rows
- * 0..kv, the multipliers of L below) and its 1-based pivot vector (LAPACK ipiv
- * convention) into host arrays h_ab (ldab * n) and h_ipiv (n). *kl, *ldab set. */
+/* ie_get_factor: copies pole i's band LU (LAPACK zgbtrf layout: column j holds rows j-kv..j+kl
+ * at offsets 0..ldab-1 with kv = 2*kl, ldab = 3*kl + 1; U in rows 0..kv, the multipliers of L
+ * below) and its 1-based pivot vector (LAPACK ipiv convention) into host arrays h_ab
+ * (ldab * n) and h_ipiv (n). *kl, *ldab set. For precision = 1 handles the factors are the
+ * complex64 ones (LAPACK cgbtrf semantics, FP32 arithmetic), widened exactly to complex128.
+ * Either array may be NULL. */
 ie_status ie_get_factor(ie_handle h, int32_t pole, ie_complex* h_ab, int32_t* h_ipiv,
                         int32_t* kl, int32_t* ldab);
 

@@ -49,6 +49,11 @@ __device__ __forceinline__ void put_c(cplx* p, cplx v) { *p = v; }
 __device__ __forceinline__ void put_c(float2* p, cplx v) {
   *p = make_float2((float)v.x, (float)v.y);
 }
+__device__ __forceinline__ cplx ld_c(const cplx* p) { return *p; }
+__device__ __forceinline__ cplx ld_c(const float2* p) {
+  const float2 v = *p;
+  return make_double2(v.x, v.y);
+}
 }  // namespace
 
 // ----------------------------------------------------------------------------------------------
@@ -73,8 +78,8 @@ void launch_dia_adjoint(const DiaDev& P, cplx* AH, cplx* BH, DiaDev* PH, cudaStr
 }
 
 // U by rows: Ut[pole][j][d-1] = U(j, j+d), d = 1..kv (zero past the matrix).
-template <typename OT>
-__global__ void u_rows_kernel(int64_t n, int64_t n_pad, int kl, int ldab, const cplx* AB, OT* Ut) {
+template <typename AT, typename OT>
+__global__ void u_rows_kernel(int64_t n, int64_t n_pad, int kl, int ldab, const AT* AB, OT* Ut) {
   const int pole = blockIdx.y;
   const int kv = 2 * kl;
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -82,7 +87,7 @@ __global__ void u_rows_kernel(int64_t n, int64_t n_pad, int kl, int ldab, const 
   const int64_t j = idx / kv;
   const int d = (int)(idx - j * kv) + 1;
   cplx v = cmk(0, 0);
-  if (j < n && j + d < n) v = AB[((int64_t)pole * n_pad + j + d) * ldab + kv - d];
+  if (j < n && j + d < n) v = ld_c(AB + ((int64_t)pole * n_pad + j + d) * ldab + kv - d);
   put_c(&Ut[((int64_t)pole * n_pad + j) * kv + d - 1], v);
 }
 
@@ -90,8 +95,15 @@ void launch_u_rows(int q, int64_t n, int64_t n_pad, int kl, int ldab, const cplx
                    float2* Ut32, cudaStream_t s) {
   const int64_t tot = n_pad * 2 * kl;
   dim3 grid((unsigned)((tot + 255) / 256), (unsigned)q);
-  if (Ut64) { u_rows_kernel<cplx><<<grid, 256, 0, s>>>(n, n_pad, kl, ldab, AB, Ut64); ie_count_launch(); }
-  if (Ut32) { u_rows_kernel<float2><<<grid, 256, 0, s>>>(n, n_pad, kl, ldab, AB, Ut32); ie_count_launch(); }
+  if (Ut64) { u_rows_kernel<cplx, cplx><<<grid, 256, 0, s>>>(n, n_pad, kl, ldab, AB, Ut64); ie_count_launch(); }
+  if (Ut32) { u_rows_kernel<cplx, float2><<<grid, 256, 0, s>>>(n, n_pad, kl, ldab, AB, Ut32); ie_count_launch(); }
+}
+
+void launch_u_rows(int q, int64_t n, int64_t n_pad, int kl, int ldab, const float2* AB,
+                   float2* Ut32, cudaStream_t s) {
+  const int64_t tot = n_pad * 2 * kl;
+  dim3 grid((unsigned)((tot + 255) / 256), (unsigned)q);
+  u_rows_kernel<float2, float2><<<grid, 256, 0, s>>>(n, n_pad, kl, ldab, AB, Ut32); ie_count_launch();
 }
 
 // Phase-2 transform of each (panel, pole), one warp: lanes 0..15 carry the values of the
@@ -99,14 +111,15 @@ void launch_u_rows(int q, int64_t n, int64_t n_pad, int kl, int ldab, const cplx
 // unit vector, column 16 + jj the dot input d_jj; the panel's steps are run in reverse
 // (jj = nvalid-1 .. 0): member j0+jj subtracts sum conj(L(r, j)) v_r over the members r in
 // (j, j+kl] and d_jj, then swaps with its pivot row. M[l][m] = final value of member l.
-__global__ void adj_transform_kernel(int64_t n, int64_t n_pad, int kl, int ldab, const cplx* AB,
+template <typename AT>
+__global__ void adj_transform_kernel(int64_t n, int64_t n_pad, int kl, int ldab, const AT* AB,
                                      const int* piv, const int* Hb, cplx* Mout, float2* M32) {
   const int P = blockIdx.x, pole = blockIdx.y, lane = threadIdx.x;
   const int kv = 2 * kl;
   const int64_t npan = n_pad / NB;
   const int64_t j0 = (int64_t)P * NB;
   const int nvalid = (int)((n - j0) < NB ? (n - j0) : NB);
-  const cplx* A = AB + (int64_t)pole * n_pad * ldab;
+  const AT* A = AB + (int64_t)pole * n_pad * ldab;
   const int* pv = piv + (int64_t)pole * n_pad;
   const int64_t base = (int64_t)pole * npan + P;
   const int* H = Hb + base * 16;
@@ -127,7 +140,7 @@ __global__ void adj_transform_kernel(int64_t n, int64_t n_pad, int kl, int ldab,
         const int64_t j = j0 + jj;
         cplx t = make_double2(0, 0);
         if (myrow > j && myrow <= j + kl && myrow < n)
-          t = cmul(cconj(A[j * ldab + kv + (myrow - j)]), val);
+          t = cmul(cconj(ld_c(A + j * ldab + kv + (myrow - j))), val);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
           t.x += __shfl_xor_sync(0xffffffffu, t.x, o);
@@ -158,7 +171,13 @@ __global__ void adj_transform_kernel(int64_t n, int64_t n_pad, int kl, int ldab,
 void launch_adj_transforms(int q, int64_t n, int64_t n_pad, int kl, int ldab, const cplx* AB,
                            const int* piv, const int* Hb, cplx* M64, float2* M32, cudaStream_t s) {
   dim3 grid((unsigned)(n_pad / NB), (unsigned)q);
-  adj_transform_kernel<<<grid, 32, 0, s>>>(n, n_pad, kl, ldab, AB, piv, Hb, M64, M32); ie_count_launch();
+  adj_transform_kernel<cplx><<<grid, 32, 0, s>>>(n, n_pad, kl, ldab, AB, piv, Hb, M64, M32); ie_count_launch();
+}
+
+void launch_adj_transforms(int q, int64_t n, int64_t n_pad, int kl, int ldab, const float2* AB,
+                           const int* piv, const int* Hb, float2* M32, cudaStream_t s) {
+  dim3 grid((unsigned)(n_pad / NB), (unsigned)q);
+  adj_transform_kernel<float2><<<grid, 32, 0, s>>>(n, n_pad, kl, ldab, AB, piv, Hb, nullptr, M32); ie_count_launch();
 }
 
 // ----------------------------------------------------------------------------------------------

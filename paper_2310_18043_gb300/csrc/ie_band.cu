@@ -47,8 +47,14 @@ void launch_spmv(const DiaDev& P, cplx aA, cplx aB, const cplx* X, int64_t ldx,
 // ----------------------------------------------------------------------------------------------
 // Assembly: AB[i][j*ldab + t] = K_i(j + t - kv, j) for t in [kl, ldab), zero fill rows t < kl,
 // zero outside the matrix and for padding columns j >= n. kv = 2 kl.
+__device__ __forceinline__ void put_c(float2* p, cplx v) { *p = make_float2((float)v.x, (float)v.y); }
+__device__ __forceinline__ void put_c(cplx* p, cplx v) { *p = v; }
+
+// K_i entries are formed in complex128 and stored in the factor precision (complex64 for the
+// mixed-precision path: the rounding of K_i itself, the first error the refinement removes).
+template <typename OT>
 __global__ void assemble_kernel(DiaDev P, const cplx* poles, int kl, int ldab, int64_t n_pad,
-                                cplx* AB) {
+                                OT* AB) {
   const int pole = blockIdx.y;
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= n_pad * ldab) return;
@@ -70,14 +76,23 @@ __global__ void assemble_kernel(DiaDev P, const cplx* poles, int kl, int ldab, i
       }
     }
   }
-  AB[(int64_t)pole * n_pad * ldab + idx] = v;
+  put_c(&AB[(int64_t)pole * n_pad * ldab + idx], v);
 }
 
-void launch_assemble(const DiaDev& P, const cplx* d_poles, int q, int kl, int ldab,
-                     int64_t n_pad, cplx* AB, cudaStream_t s) {
+template <typename OT>
+static void assemble_t(const DiaDev& P, const cplx* d_poles, int q, int kl, int ldab,
+                       int64_t n_pad, OT* AB, cudaStream_t s) {
   const int64_t tot = n_pad * ldab;
   dim3 grid((unsigned)((tot + 255) / 256), (unsigned)q);
-  assemble_kernel<<<grid, 256, 0, s>>>(P, d_poles, kl, ldab, n_pad, AB); ie_count_launch();
+  assemble_kernel<OT><<<grid, 256, 0, s>>>(P, d_poles, kl, ldab, n_pad, AB); ie_count_launch();
+}
+void launch_assemble(const DiaDev& P, const cplx* d_poles, int q, int kl, int ldab,
+                     int64_t n_pad, cplx* AB, cudaStream_t s) {
+  assemble_t(P, d_poles, q, kl, ldab, n_pad, AB, s);
+}
+void launch_assemble(const DiaDev& P, const cplx* d_poles, int q, int kl, int ldab,
+                     int64_t n_pad, float2* AB, cudaStream_t s) {
+  assemble_t(P, d_poles, q, kl, ldab, n_pad, AB, s);
 }
 
 // ----------------------------------------------------------------------------------------------
@@ -157,26 +172,51 @@ __device__ bool lu_wait_flag(const unsigned* flag, unsigned want, int* status) {
   return s_ok != 0;
 }
 
+// Element arithmetic of the band LU for complex128 and complex64 (FP32 accumulation).
+__device__ __forceinline__ double lu_abs1(cplx a) { return fabs(a.x) + fabs(a.y); }
+__device__ __forceinline__ float lu_abs1(float2 a) { return fabsf(a.x) + fabsf(a.y); }
+__device__ __forceinline__ cplx lu_mul(cplx a, cplx b) { return cmul(a, b); }
+__device__ __forceinline__ float2 lu_mul(float2 a, float2 b) {
+  return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+__device__ __forceinline__ cplx lu_fms(cplx a, cplx b, cplx c) { return cfms(a, b, c); }
+__device__ __forceinline__ float2 lu_fms(float2 a, float2 b, float2 c) {   // c - a*b
+  return make_float2(fmaf(-a.x, b.x, fmaf(a.y, b.y, c.x)), fmaf(-a.x, b.y, fmaf(-a.y, b.x, c.y)));
+}
+__device__ __forceinline__ cplx lu_rcp(cplx b) { return crcp(b); }
+// 1/b by Smith's algorithm (R. L. Smith, CACM 5(8), 1962), in FP32
+__device__ __forceinline__ float2 lu_rcp(float2 b) {
+  if (fabsf(b.x) >= fabsf(b.y)) {
+    const float r = b.y / b.x, d = b.x + b.y * r;
+    return make_float2(1.0f / d, -r / d);
+  }
+  const float r = b.x / b.y, d = b.y + b.x * r;
+  return make_float2(r / d, -1.0f / d);
+}
+template <typename CT> __device__ __forceinline__ CT lu_zero() { return CT{}; }
+
+template <typename CT>
 __global__ void __launch_bounds__(512) band_lu_kernel(int64_t n, int kl, int ldab, int64_t n_pad,
-                                                      cplx* AB, int* piv, cplx* dinv,
-                                                      cplx* ring, int* ring_tp,
+                                                      CT* AB, int* piv, CT* dinv,
+                                                      CT* ring, int* ring_tp,
                                                       unsigned* ring_flag, int R, int* status,
                                                       int P, int nown_max, int64_t skip_publish) {
+  using RT = decltype(lu_abs1(CT{}));
   const int pole = blockIdx.x / P, b = blockIdx.x % P;
   const int T = blockDim.x, tid = threadIdx.x;
   const int kv = 2 * kl;
-  cplx* A = AB + (int64_t)pole * n_pad * ldab;
+  CT* A = AB + (int64_t)pole * n_pad * ldab;
   int* pv_out = piv + (int64_t)pole * n_pad;
-  cplx* di_out = dinv + (int64_t)pole * n_pad;
-  cplx* rmul = ring + (int64_t)pole * R * (kl + 1);
+  CT* di_out = dinv + (int64_t)pole * n_pad;
+  CT* rmul = ring + (int64_t)pole * R * (kl + 1);
   int* rtp = ring_tp + (int64_t)pole * R;
   unsigned* rflag = ring_flag + (int64_t)pole * R;
-  extern __shared__ double2 lu_sm[];
-  cplx* mult = lu_sm;                // kl+1: multipliers of the current step
-  cplx* col = mult + (kl + 1);       // kl+1: pivot column of the next step (owner)
-  cplx* urow = col + (kl + 1);       // nown_max
-  cplx* arow = urow + nown_max;      // nown_max
-  __shared__ double red_v[32];
+  extern __shared__ __align__(16) unsigned char lu_sm_raw[];
+  CT* mult = (CT*)lu_sm_raw;         // kl+1: multipliers of the current step
+  CT* col = mult + (kl + 1);         // kl+1: pivot column of the next step (owner)
+  CT* urow = col + (kl + 1);         // nown_max
+  CT* arow = urow + nown_max;        // nown_max
+  __shared__ RT red_v[32];
   __shared__ int red_i[32];
   __shared__ int s_tp;
 
@@ -185,24 +225,24 @@ __global__ void __launch_bounds__(512) band_lu_kernel(int64_t n, int kl, int lda
   // col[0..pre) already holds rows jc..jc+pre-1 of the column (the look-ahead update)
   auto pivot_publish = [&](int64_t jc, int pre) {
     const int nr = (int)((n - 1 - jc) < (int64_t)kl ? (n - 1 - jc) : (int64_t)kl);
-    cplx* cj = A + jc * ldab + kv;
-    double best = -1.0;
+    CT* cj = A + jc * ldab + kv;
+    RT best = -1;
     int bi = 0;
     for (int t = tid; t <= nr; t += T) {
-      const cplx v = (t < pre) ? col[t] : __ldcg(cj + t);
+      const CT v = (t < pre) ? col[t] : __ldcg(cj + t);
       col[t] = v;
-      const double a = cabs1(v);
+      const RT a = lu_abs1(v);
       if (a > best) { best = a; bi = t; }
     }
     for (int o = 16; o > 0; o >>= 1) {   // argmax, first index on ties
-      const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+      const RT ob = __shfl_xor_sync(0xffffffffu, best, o);
       const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
       if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
     }
     if ((tid & 31) == 0) { red_v[tid >> 5] = best; red_i[tid >> 5] = bi; }
     __syncthreads();
     if (tid == 0) {
-      double bb = red_v[0];
+      RT bb = red_v[0];
       int ii = red_i[0];
       for (int w = 1; w < (T + 31) / 32; ++w)
         if (red_v[w] > bb || (red_v[w] == bb && red_i[w] < ii)) { bb = red_v[w]; ii = red_i[w]; }
@@ -210,15 +250,15 @@ __global__ void __launch_bounds__(512) band_lu_kernel(int64_t n, int kl, int lda
     }
     __syncthreads();
     const int tp = s_tp;
-    const cplx pv = col[tp];
-    const bool zero = (pv.x == 0.0 && pv.y == 0.0);
-    const cplx rcp = zero ? cmk(0, 0) : crcp(pv);
-    cplx* slot = rmul + (int64_t)(jc % R) * (kl + 1);
+    const CT pv = col[tp];
+    const bool zero = (pv.x == 0 && pv.y == 0);
+    const CT rcp = zero ? lu_zero<CT>() : lu_rcp(pv);
+    CT* slot = rmul + (int64_t)(jc % R) * (kl + 1);
     for (int t = tid; t <= nr; t += T) {
       if (t == 0) {
         cj[0] = pv;
       } else {
-        const cplx m = zero ? cmk(0, 0) : cmul((t == tp) ? col[0] : col[t], rcp);
+        const CT m = zero ? lu_zero<CT>() : lu_mul((t == tp) ? col[0] : col[t], rcp);
         cj[t] = m;
         slot[t] = m;
       }
@@ -242,7 +282,7 @@ __global__ void __launch_bounds__(512) band_lu_kernel(int64_t n, int kl, int lda
     // (a) step j's pivot offset and multipliers, published by the owner of column j
     if (!lu_wait_flag(rflag + (j % R), (unsigned)(j + 1), status)) return;
     const int nrows = (int)((n - 1 - j) < (int64_t)kl ? (n - 1 - j) : (int64_t)kl);
-    const cplx* slot = rmul + (int64_t)(j % R) * (kl + 1);
+    const CT* slot = rmul + (int64_t)(j % R) * (kl + 1);
     for (int t = 1 + tid; t <= nrows; t += T) mult[t] = __ldcg(slot + t);
     const int tp = __ldcg(rtp + (j % R));
     { const int64_t cand = (j + kl + tp < n - 1) ? (j + kl + tp) : (n - 1); if (cand > ju) ju = cand; }
@@ -252,14 +292,14 @@ __global__ void __launch_bounds__(512) band_lu_kernel(int64_t n, int kl, int lda
     if (own_next) {
       int pre = 0;
       if (j + 1 <= ju && nrows > 0) {
-        cplx* cl = A + (j + 1) * ldab + kv - 1;      // row j of column j+1
-        const cplx u = __ldcg(cl + tp), a0 = __ldcg(cl);
+        CT* cl = A + (j + 1) * ldab + kv - 1;        // row j of column j+1
+        const CT u = __ldcg(cl + tp), a0 = __ldcg(cl);
         __syncthreads();                             // rows j and j+tp read before rewritten
         for (int t = tid; t <= nrows; t += T) {
           if (t == 0) {
             cl[0] = u;
           } else {
-            const cplx nv = cfms(mult[t], u, (t == tp) ? a0 : __ldcg(cl + t));
+            const CT nv = lu_fms(mult[t], u, (t == tp) ? a0 : __ldcg(cl + t));
             cl[t] = nv;
             col[t - 1] = nv;                         // row j+t = row (j+1)+(t-1) of the column
           }
@@ -275,7 +315,7 @@ __global__ void __launch_bounds__(512) band_lu_kernel(int64_t n, int kl, int lda
     const int nown = (l0 <= ju && nrows >= 0) ? (int)((ju - l0) / P + 1) : 0;
     for (int idx = tid; idx < nown; idx += T) {
       const int64_t l = l0 + (int64_t)idx * P;
-      const cplx* cl = A + l * ldab + kv - (l - j);   // row j of column l
+      const CT* cl = A + l * ldab + kv - (l - j);     // row j of column l
       urow[idx] = __ldcg(cl + tp);
       arow[idx] = __ldcg(cl);
     }
@@ -285,8 +325,8 @@ __global__ void __launch_bounds__(512) band_lu_kernel(int64_t n, int kl, int lda
       constexpr int LU_BATCH = 8;
       const int tot = nrows * nown;
       for (int it0 = tid; it0 < tot; it0 += T * LU_BATCH) {
-        cplx val[LU_BATCH];
-        cplx* dst[LU_BATCH];
+        CT val[LU_BATCH];
+        CT* dst[LU_BATCH];
         int tt[LU_BATCH], ii[LU_BATCH];
 #pragma unroll
         for (int u = 0; u < LU_BATCH; ++u) {
@@ -304,7 +344,7 @@ __global__ void __launch_bounds__(512) band_lu_kernel(int64_t n, int kl, int lda
         }
 #pragma unroll
         for (int u = 0; u < LU_BATCH; ++u)
-          if (ii[u] >= 0) *dst[u] = cfms(mult[tt[u]], urow[ii[u]], val[u]);
+          if (ii[u] >= 0) *dst[u] = lu_fms(mult[tt[u]], urow[ii[u]], val[u]);
       }
     }
     for (int idx = tid; idx < nown; idx += T) {
@@ -323,9 +363,10 @@ int band_lu_ring_slots(int q) {
   return 2 * (pmax > 1 ? pmax : 1) + 2;
 }
 
-cudaError_t launch_band_lu(int q, int64_t n, int kl, int ldab, int64_t n_pad, cplx* AB,
-                           int* piv, cplx* dinv, cplx* ring, int* ring_tp, unsigned* ring_flag,
-                           int R, int* status, cudaStream_t s, int* ctas_per_pole) {
+template <typename CT>
+static cudaError_t band_lu_t(int q, int64_t n, int kl, int ldab, int64_t n_pad, CT* AB, int* piv,
+                             CT* dinv, CT* ring, int* ring_tp, unsigned* ring_flag, int R,
+                             int* status, cudaStream_t s, int* ctas_per_pole) {
   int dev = 0, sms = 0, per_sm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -338,15 +379,16 @@ cudaError_t launch_band_lu(int q, int64_t n, int kl, int ldab, int64_t n_pad, cp
   if (P > R - 2) P = R - 2;
   if (P < 1) return cudaErrorInvalidValue;
   int nown_max = (kv + P - 1) / P + 1;
-  size_t smem = (size_t)(2 * (kl + 1) + 2 * nown_max) * sizeof(cplx);
-  if (smem > 48 * 1024) ie_smem_optin((const void*)band_lu_kernel);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, band_lu_kernel, 512, smem);
+  size_t smem = (size_t)(2 * (kl + 1) + 2 * nown_max) * sizeof(CT);
+  auto kfn = band_lu_kernel<CT>;
+  if (smem > 48 * 1024) ie_smem_optin((const void*)kfn);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kfn, 512, smem);
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
   while ((int64_t)P * q > (int64_t)per_sm * sms && P > 1) {
     --P;
     nown_max = (kv + P - 1) / P + 1;
   }
-  smem = (size_t)(2 * (kl + 1) + 2 * nown_max) * sizeof(cplx);
+  smem = (size_t)(2 * (kl + 1) + 2 * nown_max) * sizeof(CT);
   if (ctas_per_pole) *ctas_per_pole = P;
   cudaMemsetAsync(ring_flag, 0, sizeof(unsigned) * (size_t)R * q, s);
   // Failure test hook: IE_TEST_SKIP_PUBLISH=j makes the owner of column j never set its flag,
@@ -357,7 +399,22 @@ cudaError_t launch_band_lu(int q, int64_t n, int kl, int ldab, int64_t n_pad, cp
   void* args[] = {&n, &kl, &ldab, &n_pad, &AB, &piv, &dinv, &ring, &ring_tp, &ring_flag, &R,
                   &status, &P, &nown_max, &skip_publish};
   ie_count_launch();
-  return cudaLaunchCooperativeKernel((void*)band_lu_kernel, dim3(q * P), dim3(512), args, smem, s);
+  return cudaLaunchCooperativeKernel((void*)kfn, dim3(q * P), dim3(512), args, smem, s);
+}
+
+cudaError_t launch_band_lu(int q, int64_t n, int kl, int ldab, int64_t n_pad, cplx* AB,
+                           int* piv, cplx* dinv, cplx* ring, int* ring_tp, unsigned* ring_flag,
+                           int R, int* status, cudaStream_t s, int* ctas_per_pole) {
+  return band_lu_t(q, n, kl, ldab, n_pad, AB, piv, dinv, ring, ring_tp, ring_flag, R, status, s,
+                   ctas_per_pole);
+}
+
+cudaError_t launch_band_lu(int q, int64_t n, int kl, int ldab, int64_t n_pad, float2* AB,
+                           int* piv, float2* dinv, float2* ring, int* ring_tp,
+                           unsigned* ring_flag, int R, int* status, cudaStream_t s,
+                           int* ctas_per_pole) {
+  return band_lu_t(q, n, kl, ldab, n_pad, AB, piv, dinv, ring, ring_tp, ring_flag, R, status, s,
+                   ctas_per_pole);
 }
 
 // ----------------------------------------------------------------------------------------------
@@ -401,12 +458,17 @@ void launch_pole_wsum(int q, int64_t n, int k, const cplx* Xp, int64_t ldx, int6
 // j = U(j-kv..j-1, j) (kv = 2 kl entries), columns contiguous per pole so that a panel of 8
 // columns is one bulk copy with 16-byte aligned start and length. complex128 (from the LU in
 // LAPACK band storage) or complex64 rounded from it (mixed precision, with 1/u_jj).
-__device__ __forceinline__ void put_c(float2* p, cplx v) { *p = make_float2((float)v.x, (float)v.y); }
-__device__ __forceinline__ void put_c(cplx* p, cplx v) { *p = v; }
+__device__ __forceinline__ cplx ld_c(const cplx* p) { return *p; }
+__device__ __forceinline__ cplx ld_c(const float2* p) {
+  const float2 v = *p;
+  return make_double2(v.x, v.y);
+}
 
-template <typename OT>
-__global__ void factors_split_kernel(int64_t n_pad, int kl, int ldab, int klp, const cplx* AB,
-                                     const cplx* dinv, OT* L32, OT* U32, OT* dinv32) {
+// Split copy of band factors (input AB in complex128 or complex64, output in OT): L column j =
+// its kl multipliers (padded to klp), U column j = U(j-kv..j-1, j); diag (nullable) = U(j,j).
+template <typename IT, typename OT>
+__global__ void factors_split_kernel(int64_t n_pad, int kl, int ldab, int klp, const IT* AB,
+                                     OT* L, OT* U, OT* diag) {
   const int pole = blockIdx.y;
   const int kv = 2 * kl;
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -414,29 +476,28 @@ __global__ void factors_split_kernel(int64_t n_pad, int kl, int ldab, int klp, c
   if (idx >= n_pad * per) return;
   const int64_t j = idx / per;
   const int t = (int)(idx - j * per);
-  const cplx* col = AB + ((int64_t)pole * n_pad + j) * ldab;
+  const IT* col = AB + ((int64_t)pole * n_pad + j) * ldab;
   if (t < klp) {
-    put_c(&L32[((int64_t)pole * n_pad + j) * klp + t], (t < kl) ? col[kv + 1 + t] : cmk(0, 0));
+    put_c(&L[((int64_t)pole * n_pad + j) * klp + t], (t < kl) ? ld_c(col + kv + 1 + t) : cmk(0, 0));
   } else if (t < klp + kv) {
-    put_c(&U32[((int64_t)pole * n_pad + j) * kv + (t - klp)], col[t - klp]);
-  } else if (dinv32) {
-    put_c(&dinv32[(int64_t)pole * n_pad + j], dinv[(int64_t)pole * n_pad + j]);
+    put_c(&U[((int64_t)pole * n_pad + j) * kv + (t - klp)], ld_c(col + t - klp));
+  } else if (diag) {
+    put_c(&diag[(int64_t)pole * n_pad + j], ld_c(col + kv));
   }
 }
 
-void launch_factors_to_c64(int q, int64_t n_pad, int kl, int ldab, int klp, const cplx* AB,
-                           const cplx* dinv, float2* L32, float2* U32, float2* dinv32,
-                           cudaStream_t s) {
+void launch_factors_split32(int q, int64_t n_pad, int kl, int ldab, int klp, const float2* AB,
+                            float2* L32, float2* U32, float2* diag32, cudaStream_t s) {
   const int64_t tot = n_pad * (klp + 2 * kl + 1);
   dim3 grid((unsigned)((tot + 255) / 256), (unsigned)q);
-  factors_split_kernel<float2><<<grid, 256, 0, s>>>(n_pad, kl, ldab, klp, AB, dinv, L32, U32, dinv32); ie_count_launch();
+  factors_split_kernel<float2, float2><<<grid, 256, 0, s>>>(n_pad, kl, ldab, klp, AB, L32, U32, diag32); ie_count_launch();
 }
 
 void launch_factors_split64(int q, int64_t n_pad, int kl, int ldab, const cplx* AB, cplx* L64,
                             cplx* U64, cudaStream_t s) {
   const int64_t tot = n_pad * (kl + 2 * kl + 1);
   dim3 grid((unsigned)((tot + 255) / 256), (unsigned)q);
-  factors_split_kernel<cplx><<<grid, 256, 0, s>>>(n_pad, kl, ldab, kl, AB, nullptr, L64, U64, (cplx*)nullptr); ie_count_launch();
+  factors_split_kernel<cplx, cplx><<<grid, 256, 0, s>>>(n_pad, kl, ldab, kl, AB, L64, U64, (cplx*)nullptr); ie_count_launch();
 }
 
 // R32[i][:, c] = (complex64) (BV[:, c] - K_i X[i][:, c]), K_i = p_i B - A, for all poles i:

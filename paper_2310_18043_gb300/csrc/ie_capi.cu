@@ -119,6 +119,8 @@ struct ie_handle_s {
   std::vector<unsigned> h_rnrm;
   int64_t refine_solves = 0;
   double refine_last_corr = 0.0;
+  float2* AB32 = nullptr;  // complex64 band LU (precision = 1), released after the split copy
+  float2* diag32 = nullptr; // q * n_pad: U(j, j) of the complex64 LU (ie_get_factor)
   float2* L32 = nullptr;   // q * n_pad * klp
   float2* U32 = nullptr;   // q * n_pad * kv
   float2* dinv32 = nullptr;
@@ -338,9 +340,9 @@ static ie_status alloc_workspace(ie_handle h) {
   return IE_OK;
 }
 
-// Adjoint pencil for ie_apply_GH / ie_solve_left, from the complex128 band factors (AB must
-// still be present): (A^H, B^H) and their norms, conj(p_i), conj(w_i), U by rows and the
-// phase-2 transforms, in the handle's factor precision.
+// Adjoint pencil for ie_apply_GH / ie_solve_left, from the band factors (AB or AB32 must still
+// be present): (A^H, B^H) and their norms, conj(p_i), conj(w_i), U by rows and the phase-2
+// transforms, in the handle's factor precision.
 static ie_status setup_adjoint(ie_handle h, cudaStream_t s) {
   const int q = h->q;
   const size_t nd = (size_t)h->ndiag * h->n, np = (size_t)(h->n_pad / 8);
@@ -373,9 +375,14 @@ static ie_status setup_adjoint(ie_handle h, cudaStream_t s) {
     CK(h->alloc(&h->Ut32, nu));
     CK(h->alloc(&h->Madj32, nm));
   }
-  launch_u_rows(q, h->n, h->n_pad, h->kl, h->ldab, h->AB, h->Ut64, h->Ut32, s);
-  launch_adj_transforms(q, h->n, h->n_pad, h->kl, h->ldab, h->AB, h->piv, h->Hb, h->Madj64,
-                        h->Madj32, s);
+  if (h->precision == 0) {
+    launch_u_rows(q, h->n, h->n_pad, h->kl, h->ldab, h->AB, h->Ut64, nullptr, s);
+    launch_adj_transforms(q, h->n, h->n_pad, h->kl, h->ldab, h->AB, h->piv, h->Hb, h->Madj64,
+                          nullptr, s);
+  } else {
+    launch_u_rows(q, h->n, h->n_pad, h->kl, h->ldab, h->AB32, h->Ut32, s);
+    launch_adj_transforms(q, h->n, h->n_pad, h->kl, h->ldab, h->AB32, h->piv, h->Hb, h->Madj32, s);
+  }
   CK(cudaStreamSynchronize(s));
   h->adj = true;
   return IE_OK;
@@ -458,10 +465,14 @@ extern "C" ie_status ie_create(const ie_pencil* pen, ie_complex center, double r
     return fail(IE_ERR_CUDA);
   h->normA = hn[0];
   h->normB = hn[1];
-  // factors
-  if (h->alloc(&h->AB, (size_t)q * h->n_pad * h->ldab) != cudaSuccess ||
+  // factors: complex128 band LU (precision 0), or the same LU in complex64 with FP32
+  // arithmetic (precision 1), from K_i assembled in the factor precision
+  const bool mixed = opts.precision == 1;
+  const size_t nab = (size_t)q * h->n_pad * h->ldab;
+  if ((mixed ? h->alloc(&h->AB32, nab) : h->alloc(&h->AB, nab)) != cudaSuccess ||
       h->alloc(&h->piv, (size_t)q * h->n_pad) != cudaSuccess ||
-      h->alloc(&h->dinv, (size_t)q * h->n_pad) != cudaSuccess ||
+      (mixed ? h->alloc(&h->dinv32, (size_t)q * h->n_pad)
+             : h->alloc(&h->dinv, (size_t)q * h->n_pad)) != cudaSuccess ||
       h->alloc(&h->lu_ring, (size_t)q * band_lu_ring_slots(q) * (kl + 1)) != cudaSuccess ||
       h->alloc(&h->lu_ring_tp, (size_t)q * band_lu_ring_slots(q)) != cudaSuccess ||
       h->alloc(&h->bar, (size_t)q * band_lu_ring_slots(q)) != cudaSuccess ||
@@ -469,15 +480,23 @@ extern "C" ie_status ie_create(const ie_pencil* pen, ie_complex center, double r
     return fail(IE_ERR_OOM);
   cudaMemsetAsync(h->status, 0, sizeof(int) * ST_COUNT, s);
   cudaMemsetAsync(h->piv, 0, sizeof(int) * (size_t)q * h->n_pad, s);
-  cudaMemsetAsync(h->dinv, 0, sizeof(cplx) * (size_t)q * h->n_pad, s);
+  if (mixed) cudaMemsetAsync(h->dinv32, 0, sizeof(float2) * (size_t)q * h->n_pad, s);
+  else cudaMemsetAsync(h->dinv, 0, sizeof(cplx) * (size_t)q * h->n_pad, s);
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
   cudaEventRecord(e0, s);
-  launch_assemble(h->P, h->d_poles, q, kl, h->ldab, h->n_pad, h->AB, s);
-  cudaError_t le = launch_band_lu(q, h->n, kl, h->ldab, h->n_pad, h->AB, h->piv, h->dinv,
-                                  h->lu_ring, h->lu_ring_tp, h->bar, band_lu_ring_slots(q),
-                                  h->status, s, &h->lu_ctas);
+  cudaError_t le;
+  if (mixed) {
+    launch_assemble(h->P, h->d_poles, q, kl, h->ldab, h->n_pad, h->AB32, s);
+    le = launch_band_lu(q, h->n, kl, h->ldab, h->n_pad, h->AB32, h->piv, h->dinv32,
+                        (float2*)h->lu_ring, h->lu_ring_tp, h->bar, band_lu_ring_slots(q),
+                        h->status, s, &h->lu_ctas);
+  } else {
+    launch_assemble(h->P, h->d_poles, q, kl, h->ldab, h->n_pad, h->AB, s);
+    le = launch_band_lu(q, h->n, kl, h->ldab, h->n_pad, h->AB, h->piv, h->dinv, h->lu_ring,
+                        h->lu_ring_tp, h->bar, band_lu_ring_slots(q), h->status, s, &h->lu_ctas);
+  }
   cudaEventRecord(e1, s);
   if (le != cudaSuccess) { cudaEventDestroy(e0); cudaEventDestroy(e1); return fail(map_err(le)); }
   if (cudaStreamSynchronize(s) != cudaSuccess) {
@@ -494,22 +513,29 @@ extern "C" ie_status ie_create(const ie_pencil* pen, ie_complex center, double r
   if (st[ST_TIMEOUT]) return fail(IE_ERR_TIMEOUT);
   {
     const size_t np = (size_t)(h->n_pad / 8);
-    if (opts.precision == 0) {   // the complex64 path has its own split copy
+    if (!mixed) {
       if (h->alloc(&h->L64, (size_t)q * h->n_pad * kl) != cudaSuccess ||
-          h->alloc(&h->U64, (size_t)q * h->n_pad * h->kv) != cudaSuccess)
+          h->alloc(&h->U64, (size_t)q * h->n_pad * h->kv) != cudaSuccess ||
+          h->alloc(&h->Tb, (size_t)q * np * 256) != cudaSuccess ||
+          h->alloc(&h->Hb, (size_t)q * np * 16) != cudaSuccess ||
+          h->alloc(&h->Uinvb, (size_t)q * np * 64) != cudaSuccess)
         return fail(IE_ERR_OOM);
       launch_factors_split64(q, h->n_pad, kl, h->ldab, h->AB, h->L64, h->U64, s);
+      launch_block_transforms(q, h->n, h->n_pad, kl, h->ldab, h->AB, h->piv, h->dinv, h->Tb,
+                              h->Hb, h->Uinvb, nullptr, nullptr, s);
+    } else {
+      if (h->alloc(&h->L32, (size_t)q * h->n_pad * h->klp) != cudaSuccess ||
+          h->alloc(&h->U32, (size_t)q * h->n_pad * h->kv) != cudaSuccess ||
+          h->alloc(&h->diag32, (size_t)q * h->n_pad) != cudaSuccess ||
+          h->alloc(&h->Hb, (size_t)q * np * 16) != cudaSuccess ||
+          h->alloc(&h->T32, (size_t)q * np * 256) != cudaSuccess ||
+          h->alloc(&h->Ub32, (size_t)q * np * 64) != cudaSuccess)
+        return fail(IE_ERR_OOM);
+      launch_factors_split32(q, h->n_pad, kl, h->ldab, h->klp, h->AB32, h->L32, h->U32,
+                             h->diag32, s);
+      launch_block_transforms(q, h->n, h->n_pad, kl, h->ldab, h->AB32, h->piv, h->dinv32, h->Hb,
+                              h->T32, h->Ub32, s);
     }
-    if (h->alloc(&h->Tb, (size_t)q * np * 256) != cudaSuccess ||
-        h->alloc(&h->Hb, (size_t)q * np * 16) != cudaSuccess ||
-        h->alloc(&h->Uinvb, (size_t)q * np * 64) != cudaSuccess)
-      return fail(IE_ERR_OOM);
-    if (opts.precision == 1 &&
-        (h->alloc(&h->T32, (size_t)q * np * 256) != cudaSuccess ||
-         h->alloc(&h->Ub32, (size_t)q * np * 64) != cudaSuccess))
-      return fail(IE_ERR_OOM);
-    launch_block_transforms(q, h->n, h->n_pad, kl, h->ldab, h->AB, h->piv, h->dinv, h->Tb, h->Hb,
-                            h->Uinvb, h->T32, h->Ub32, s);
     if (cudaStreamSynchronize(s) != cudaSuccess) return fail(IE_ERR_CUDA);
     if (opts.adjoint) {
       ie_status as = setup_adjoint(h, s);
@@ -518,23 +544,17 @@ extern "C" ie_status ie_create(const ie_pencil* pen, ie_complex center, double r
   }
   ie_status ws = alloc_workspace(h);
   if (ws != IE_OK) return fail(ws);
-  if (h->precision == 1) {
+  if (mixed) {
     const size_t nk = (size_t)h->n * h->kmax;
-    if (h->alloc(&h->L32, (size_t)q * h->n_pad * h->klp) != cudaSuccess ||
-        h->alloc(&h->U32, (size_t)q * h->n_pad * h->kv) != cudaSuccess ||
-        h->alloc(&h->dinv32, (size_t)q * h->n_pad) != cudaSuccess ||
-        h->alloc(&h->Y32, (size_t)q * nk) != cudaSuccess ||
+    if (h->alloc(&h->Y32, (size_t)q * nk) != cudaSuccess ||
         h->alloc(&h->R32, (size_t)q * nk) != cudaSuccess ||
         h->alloc(&h->BV32, nk) != cudaSuccess ||
         h->alloc(&h->d_rnrm, (size_t)q * h->kmax * 2) != cudaSuccess)
       return fail(IE_ERR_OOM);
     h->h_rnrm.assign((size_t)q * h->kmax * 2, 0u);
-    launch_factors_to_c64(q, h->n_pad, kl, h->ldab, h->klp, h->AB, h->dinv, h->L32, h->U32,
-                          h->dinv32, s);
-    if (cudaStreamSynchronize(s) != cudaSuccess) return fail(IE_ERR_CUDA);
-    // the complex128 band factors are no longer used by this handle
-    h->release(h->AB);
-    h->AB = nullptr;
+    // the band storage of the complex64 LU is no longer used: the split copy serves the solves
+    h->release(h->AB32);
+    h->AB32 = nullptr;
   }
   if (cudaGetLastError() != cudaSuccess) return fail(IE_ERR_CUDA);
   *out = h;
@@ -1319,12 +1339,31 @@ extern "C" ie_status ie_get_coeffs(ie_handle h, ie_complex* h_poles, ie_complex*
 
 extern "C" ie_status ie_get_factor(ie_handle h, int32_t pole, ie_complex* h_ab, int32_t* h_ipiv,
                                    int32_t* kl, int32_t* ldab) {
-  if (!h || pole < 0 || pole >= h->q || !h->AB) return IE_ERR_ARG;
+  if (!h || pole < 0 || pole >= h->q || (!h->AB && !h->L32)) return IE_ERR_ARG;
   if (kl) *kl = h->kl;
   if (ldab) *ldab = h->ldab;
-  if (h_ab)
+  if (h_ab && h->AB) {
     CK(cudaMemcpy(h_ab, h->AB + (int64_t)pole * h->n_pad * h->ldab,
                   sizeof(cplx) * (size_t)h->n * h->ldab, cudaMemcpyDeviceToHost));
+  } else if (h_ab) {
+    // complex64 factors, widened exactly: L from L32, U above the diagonal from U32, U(j,j)
+    const int64_t n = h->n, np = h->n_pad;
+    const int k_l = h->kl, kv = h->kv, ld = h->ldab, klp = h->klp;
+    std::vector<float2> L((size_t)np * klp), U((size_t)np * kv), D((size_t)np);
+    CK(cudaMemcpy(L.data(), h->L32 + (int64_t)pole * np * klp, sizeof(float2) * L.size(),
+                  cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(U.data(), h->U32 + (int64_t)pole * np * kv, sizeof(float2) * U.size(),
+                  cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(D.data(), h->diag32 + (int64_t)pole * np, sizeof(float2) * D.size(),
+                  cudaMemcpyDeviceToHost));
+    for (int64_t j = 0; j < n; ++j) {
+      ie_complex* col = h_ab + j * ld;
+      for (int t = 0; t < ld; ++t) col[t] = ie_complex{0.0, 0.0};
+      for (int t = 0; t < kv; ++t) col[t] = ie_complex{U[j * kv + t].x, U[j * kv + t].y};
+      col[kv] = ie_complex{D[j].x, D[j].y};
+      for (int t = 0; t < k_l; ++t) col[kv + 1 + t] = ie_complex{L[j * klp + t].x, L[j * klp + t].y};
+    }
+  }
   if (h_ipiv) {
     CK(cudaMemcpy(h_ipiv, h->piv + (int64_t)pole * h->n_pad, sizeof(int) * (size_t)h->n,
                   cudaMemcpyDeviceToHost));

@@ -100,15 +100,23 @@ struct DiaDev {
 // when xoff != nullptr, else at X + c*ldx. Y column c at Y + c*ldy.
 void launch_spmv(const DiaDev& P, cplx alphaA, cplx alphaB, const cplx* X, int64_t ldx,
                  const int64_t* xoff, int k, cplx* Y, int64_t ldy, cudaStream_t s);
-// Assemble K_i = p_i B - A into LAPACK band storage for all q poles (columns >= n zeroed).
+// Assemble K_i = p_i B - A into LAPACK band storage for all q poles (columns >= n zeroed),
+// in complex128 or (mixed precision) complex64.
 void launch_assemble(const DiaDev& P, const cplx* d_poles, int q, int kl, int ldab,
                      int64_t n_pad, cplx* AB, cudaStream_t s);
+void launch_assemble(const DiaDev& P, const cplx* d_poles, int q, int kl, int ldab,
+                     int64_t n_pad, float2* AB, cudaStream_t s);
 // Batched band LU with partial pivoting, all q poles in one cooperative launch.
 // Ring slots per pole for the LU's published pivots (> the CTAs per pole it will use).
 int band_lu_ring_slots(int q);
 cudaError_t launch_band_lu(int q, int64_t n, int kl, int ldab, int64_t n_pad, cplx* AB,
                            int* piv, cplx* dinv, cplx* ring, int* ring_tp, unsigned* ring_flag,
                            int R, int* status, cudaStream_t s, int* ctas_per_pole);
+// The same factorisation in complex64 with FP32 arithmetic (the mixed-precision path).
+cudaError_t launch_band_lu(int q, int64_t n, int kl, int ldab, int64_t n_pad, float2* AB,
+                           int* piv, float2* dinv, float2* ring, int* ring_tp,
+                           unsigned* ring_flag, int R, int* status, cudaStream_t s,
+                           int* ctas_per_pole);
 // Forward (P, L) then backward (U) band solves for all q poles and k RHS columns;
 // Xp[i] (n x k, ld = ldx, pole stride xstride) = w_i K_i^{-1} RHS.
 // L64/U64: the split complex128 factors (launch_factors_split64); Tb/Hb/Ub: the per-panel
@@ -124,6 +132,10 @@ cudaError_t launch_band_solve(int q, int64_t n, int kl, int64_t n_pad, const cpl
 void launch_block_transforms(int q, int64_t n, int64_t n_pad, int kl, int ldab, const cplx* AB,
                              const int* piv, const cplx* dinv, cplx* T, int* H, cplx* Ui,
                              float2* T32, float2* Ui32, cudaStream_t s);
+// The same from the complex64 band LU: complex64 T32, Ui32 (formed in FP64, rounded) and H.
+void launch_block_transforms(int q, int64_t n, int64_t n_pad, int kl, int ldab, const float2* AB,
+                             const int* piv, const float2* dinv, int* H, float2* T32,
+                             float2* Ui32, cudaStream_t s);
 // Mixed precision: complex64 band solves; X (FP64, per pole) = x (accumulate = 0), or
 // (accumulate = 1) x is written in place over the forward result in Y32 and X is untouched.
 // RHS column c of pole i at RHS + i*rstride + c*ldr (rstride 0: shared right-hand side).
@@ -137,9 +149,10 @@ cudaError_t launch_band_solve32(int q, int64_t n, int kl, int64_t n_pad, const f
 // complex128 split copy: L64 (n_pad x kl per pole), U64 (n_pad x 2kl per pole)
 void launch_factors_split64(int q, int64_t n_pad, int kl, int ldab, const cplx* AB, cplx* L64,
                             cplx* U64, cudaStream_t s);
-void launch_factors_to_c64(int q, int64_t n_pad, int kl, int ldab, int klp, const cplx* AB,
-                           const cplx* dinv, float2* L32, float2* U32, float2* dinv32,
-                           cudaStream_t s);
+// complex64 split copy from the complex64 band LU: L32 (n_pad x klp per pole), U32 (n_pad x
+// 2kl per pole) and diag32 = U(j, j) (n_pad per pole; nullable)
+void launch_factors_split32(int q, int64_t n_pad, int kl, int ldab, int klp, const float2* AB,
+                            float2* L32, float2* U32, float2* diag32, cudaStream_t s);
 void launch_pole_residual(const DiaDev& P, const cplx* d_poles, int q, int k, const cplx* BV,
                           int64_t ldb, const cplx* X, int64_t ldx, int64_t xstride, float2* R32,
                           int64_t ldr, int64_t rstride, cudaStream_t s);
@@ -230,10 +243,14 @@ void launch_dia_adjoint(const DiaDev& P, cplx* AH, cplx* BH, DiaDev* PH, cudaStr
 // U by rows from the band LU: row j's U(j, j+1..j+2kl) at Ut + (pole*n_pad + j)*2kl.
 void launch_u_rows(int q, int64_t n, int64_t n_pad, int kl, int ldab, const cplx* AB, cplx* Ut64,
                    float2* Ut32, cudaStream_t s);
+void launch_u_rows(int q, int64_t n, int64_t n_pad, int kl, int ldab, const float2* AB,
+                   float2* Ut32, cudaStream_t s);
 // Per (pole, 8-row panel): the 16x24 transform of the conjugate-transpose L sweep on the
 // members Hb (complex128 into M64; complex64 copy when M32 != null).
 void launch_adj_transforms(int q, int64_t n, int64_t n_pad, int kl, int ldab, const cplx* AB,
                            const int* piv, const int* Hb, cplx* M64, float2* M32, cudaStream_t s);
+void launch_adj_transforms(int q, int64_t n, int64_t n_pad, int kl, int ldab, const float2* AB,
+                           const int* piv, const int* Hb, float2* M32, cudaStream_t s);
 // Xp[i] = conj(w_i) K_i^{-H} RHS for all q poles (complex128 factors).
 cudaError_t launch_band_solve_adj(int q, int64_t n, int kl, int64_t n_pad, const cplx* L64,
                                   const cplx* Ut64, const cplx* Ub, const cplx* M64, const int* Hb,

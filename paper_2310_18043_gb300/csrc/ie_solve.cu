@@ -61,6 +61,17 @@ struct SolveArgsT {
 // REGS: register budget. The register file is split over the SM's 4 sub-partitions (16K
 // registers each) and a block's warps are spread over them, so a block of W warps needs
 // ceil(W/4) * 32 * REGS <= 16384: 112 registers allow 16 warps, 96 allow 20.
+//
+// Window layout. The rows a panel's columns update are held in registers, one row per slot
+// (SPT slots per thread); the NB head rows being solved live in shared memory (hd). Forward:
+// the panel with head rows j0..j0+NB-1 updates rows j0+NB..j0+NB+kl-1, so the window has
+// Sf = max(kl, NB) slots (slot = (row - NB) mod Sf). Backward: the panel with head rows
+// j0-NB+1..j0 updates rows j0-NB-kv+1..j0-NB, so Sb = max(kv, NB) slots (slot =
+// (n_pad-1-NB - row) mod Sb). After a panel's update the window's NB rows nearest the head
+// become the next head: they move to hd and their slots take the rows entering the window
+// (S rows further on, not yet touched by any solved column). Keeping the head out of the
+// register window makes the thread count S / SPT (a multiple of 4 warps for kl = 256 or
+// 512), so every sub-partition of the SM gets the same share of the update.
 template <typename CT, int NC, int SPT, int REGS>
 __global__ void __maxnreg__(REGS) band_solve_kernel(SolveArgsT<CT> a) {
   const int pole = blockIdx.y;
@@ -71,8 +82,6 @@ __global__ void __maxnreg__(REGS) band_solve_kernel(SolveArgsT<CT> a) {
   const int64_t n = a.n;
   const CT* Lp = a.L + (int64_t)pole * a.lstride;
   const CT* Up = a.U + (int64_t)pole * a.ustride;
-  const int* pivp = a.piv + (int64_t)pole * a.n_pad;
-  const CT* dinvp = a.dinv + (int64_t)pole * a.n_pad;
   const int64_t npan = a.n_pad / NB;
   const CT* Tp = a.Tb + (int64_t)pole * npan * 256;
   const int* Hp = a.Hb + (int64_t)pole * npan * 16;
@@ -85,8 +94,7 @@ __global__ void __maxnreg__(REGS) band_solve_kernel(SolveArgsT<CT> a) {
 
   extern __shared__ __align__(128) unsigned char sm_raw[];
   uint64_t* mbar = (uint64_t*)sm_raw;                          // nstage mbarriers
-  CT* bc = (CT*)(sm_raw + 128);                                // [2][2][NC] broadcast cells
-  CT* hd = bc + 4 * NC;                                        // [NB][NC] head values
+  CT* hd = (CT*)(sm_raw + 128);                                // [NB][NC] head values
   CT* xs = hd + NB * NC;                                       // [NB][NC] solved head
   CT* hv = xs + NB * NC;                                       // [16][NC] forward set H
   CT* hv2 = hv + 16 * NC;                                      // [16][NC] T H
@@ -106,6 +114,8 @@ __global__ void __maxnreg__(REGS) band_solve_kernel(SolveArgsT<CT> a) {
       return;
     }
   }
+  // the last warp issues the bulk copies, so that warp 0 (head solves) never waits on it
+  const int issuer = T - 32;
 
   if (tid == 0) {
     s_fail = 0;
@@ -116,12 +126,12 @@ __global__ void __maxnreg__(REGS) band_solve_kernel(SolveArgsT<CT> a) {
 
   const int64_t npanel = a.n_pad / NB;
   // ------------------------------- forward: P L y = rhs -------------------------------------
-  // Block = panel P, steps j0..j0+NB-1 (j0 = P*NB). Window of Sf = kl + NB rows j0..j0+Sf-1
-  // (slot = row mod Sf). Within a block only the NB head rows and the block's pivot rows take
-  // part in swaps; on that set H (16 members) the block's swaps and eliminations are the fixed
-  // 16x16 matrix T (precomputed from the factors), so: (A) gather H, (B) H <- T H in
-  // parallel, (C) head rows leave with y, pivot members take their values, every other row
-  // applies the block's NB multipliers at once. Three barriers per NB rows.
+  // Panel P, steps j0..j0+NB-1 (j0 = P*NB). Only the NB head rows and the panel's pivot rows
+  // take part in swaps; on that set H (16 members) the panel's swaps and eliminations are the
+  // fixed 16x16 matrix T (precomputed from the factors), so: (A) gather H (head rows from hd,
+  // pivot members from the window), (B) H <- T H in parallel, the head rows leave with y,
+  // (C) pivot members take their values, every other window row applies the panel's NB
+  // multipliers at once, and the window's first NB rows move to hd. Three barriers per panel.
   auto issue_fwd = [&](int64_t P, int st) {
     unsigned char* dst = stage0 + (size_t)st * stage_bytes;
     const uint32_t bar = smem_u32(&mbar[st]);
@@ -132,19 +142,24 @@ __global__ void __maxnreg__(REGS) band_solve_kernel(SolveArgsT<CT> a) {
     bulk_g2s(smem_u32(dst + fwd_cols_bytes + 256 * sizeof(CT)), Hp + P * 16,
              (uint32_t)(16 * sizeof(int)), bar);
   };
-  const int Sf = kl + NB;
+  const int Sf = kl > NB ? kl : NB;
   CT v[SPT][NC], nxt[SPT][NC];
   int64_t frow[SPT];
-  if (tid == 0)
+  if (tid == issuer)
     for (int st = 0; st < a.nstage && st < npanel; ++st) issue_fwd(st, st);
+  for (int e = tid; e < NB * NC; e += T) {
+    const int t = e / NC, c = e - (e / NC) * NC;
+    hd[e] = (t < n && c < ncol) ? R[(int64_t)(c0 + c) * a.ldr + t] : zero;
+  }
 #pragma unroll
   for (int u = 0; u < SPT; ++u) {
     const int s = tid + u * T;
-    frow[u] = s;
+    const int64_t r = NB + s;
+    frow[u] = r;
 #pragma unroll
     for (int c = 0; c < NC; ++c) {
-      v[u][c] = (s < Sf && s < n && c < ncol) ? R[(int64_t)(c0 + c) * a.ldr + s] : zero;
-      nxt[u][c] = (s < Sf && s + Sf < n && c < ncol) ? R[(int64_t)(c0 + c) * a.ldr + s + Sf] : zero;
+      v[u][c] = (s < Sf && r < n && c < ncol) ? R[(int64_t)(c0 + c) * a.ldr + r] : zero;
+      nxt[u][c] = (s < Sf && r + Sf < n && c < ncol) ? R[(int64_t)(c0 + c) * a.ldr + r + Sf] : zero;
     }
   }
   bool failed = false;
@@ -154,15 +169,15 @@ __global__ void __maxnreg__(REGS) band_solve_kernel(SolveArgsT<CT> a) {
     __syncthreads();
     if (s_fail) { failed = true; break; }
     // the previous panel's stage is free: refill it
-    if (tid == 0 && P >= 1 && P - 1 + a.nstage < npanel)
+    if (tid == issuer && P >= 1 && P - 1 + a.nstage < npanel)
       issue_fwd(P - 1 + a.nstage, (int)((P - 1) % a.nstage));
     const CT* Lst = (const CT*)(stage0 + (size_t)st * stage_bytes);
     const CT* Tst = (const CT*)(stage0 + (size_t)st * stage_bytes + fwd_cols_bytes);
     const int* Hst = (const int*)(stage0 + (size_t)st * stage_bytes + fwd_cols_bytes + 256 * sizeof(CT));
     const int64_t j0 = P * NB;
     const int nvalid = (int)((n - j0) < NB ? (n - j0) : NB);
-    // (A) gather the members' values; a slot's member index: head rows by arithmetic, pivot
-    // members by comparing with H's last 8 entries
+    // (A) gather: head rows from hd, pivot members (H entries NB..15) from the window
+    for (int e = tid; e < NB * NC; e += T) hv[e] = hd[e];
     int mem[SPT];
 #pragma unroll
     for (int u = 0; u < SPT; ++u) {
@@ -170,20 +185,16 @@ __global__ void __maxnreg__(REGS) band_solve_kernel(SolveArgsT<CT> a) {
       mem[u] = -1;
       if (s >= Sf) continue;
       const int dr = (int)(frow[u] - j0);   // row offset from the panel head (32-bit)
-      if (dr >= 0 && dr < NB) {
-        mem[u] = dr;
-      } else {
-        const int j0i = (int)j0;
+      const int j0i = (int)j0;
 #pragma unroll
-        for (int i = NB; i < 16; ++i)
-          if (Hst[i] - j0i == dr) mem[u] = i;
-      }
+      for (int i = NB; i < 16; ++i)
+        if (Hst[i] - j0i == dr) mem[u] = i;
       if (mem[u] >= 0)
 #pragma unroll
         for (int c = 0; c < NC; ++c) hv[mem[u] * NC + c] = v[u][c];
     }
     __syncthreads();
-    // (B) H <- T H
+    // (B) H <- T H; the head rows' results are final: y
     for (int e = tid; e < 16 * NC; e += T) {
       const int i = e / NC, c = e - (e / NC) * NC;
       if (Hst[i] >= 0) {
@@ -191,6 +202,7 @@ __global__ void __maxnreg__(REGS) band_solve_kernel(SolveArgsT<CT> a) {
         for (int m = 0; m < 16; ++m)
           if (Hst[m] >= 0) acc = cfma(Tst[i * 16 + m], hv[m * NC + c], acc);
         hv2[i * NC + c] = acc;
+        if (i < nvalid && c < ncol) Yo[(int64_t)(c0 + c) * a.ldy + j0 + i] = acc;
       }
     }
     __syncthreads();
@@ -201,19 +213,7 @@ __global__ void __maxnreg__(REGS) band_solve_kernel(SolveArgsT<CT> a) {
       if (s >= Sf) continue;
       const int64_t r = frow[u];
       const int i = mem[u];
-      if (i >= 0 && i < NB) {
-        if (r < n)
-#pragma unroll
-          for (int c = 0; c < NC; ++c)
-            if (c < ncol) Yo[(int64_t)(c0 + c) * a.ldy + r] = hv2[i * NC + c];
-        const int64_t r2 = r + Sf;
-        frow[u] = r2;
-#pragma unroll
-        for (int c = 0; c < NC; ++c) {
-          v[u][c] = nxt[u][c];
-          nxt[u][c] = (r2 + Sf < n && c < ncol) ? R[(int64_t)(c0 + c) * a.ldr + r2 + Sf] : zero;
-        }
-      } else if (i >= NB) {
+      if (i >= NB) {
 #pragma unroll
         for (int c = 0; c < NC; ++c) v[u][c] = hv2[i * NC + c];
       } else {
@@ -221,11 +221,24 @@ __global__ void __maxnreg__(REGS) band_solve_kernel(SolveArgsT<CT> a) {
 #pragma unroll
         for (int jj = 0; jj < NB; ++jj) {
           const int dd = dr - jj;               // row - (j0 + jj)
-          if (jj < nvalid && dd > 0 && dd <= kl) {
+          if (jj < nvalid && dd <= kl) {        // dd >= NB - jj >= 1 for every window row
             const CT lv = Lst[jj * klp + dd - 1];
 #pragma unroll
             for (int c = 0; c < NC; ++c) v[u][c] = cfms(lv, hv2[jj * NC + c], v[u][c]);
           }
+        }
+      }
+      // rows j0+NB..j0+2NB-1 are the next panel's head: to hd, and the slot takes row r + Sf
+      const int dh = (int)(r - j0) - NB;
+      if (dh < NB) {
+#pragma unroll
+        for (int c = 0; c < NC; ++c) hd[dh * NC + c] = v[u][c];
+        const int64_t r2 = r + Sf;
+        frow[u] = r2;
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+          v[u][c] = nxt[u][c];
+          nxt[u][c] = (r2 + Sf < n && c < ncol) ? R[(int64_t)(c0 + c) * a.ldr + r2 + Sf] : zero;
         }
       }
     }
@@ -248,9 +261,10 @@ __global__ void __maxnreg__(REGS) band_solve_kernel(SolveArgsT<CT> a) {
   }
   __syncthreads();
   // ------------------------------- backward: U x = y (blocked) -------------------------------
-  // Block = panel Bp, top row j0 = n_pad - 1 - Bp*NB; window of Sb = kv + NB rows
-  // j0-Sb+1..j0 (slot = row mod Sb). Rows >= n are virtual: zero values, zero factor
-  // columns, zero 1/u_jj.
+  // Panel Bp, head rows j0-NB+1..j0 (j0 = n_pad - 1 - Bp*NB) in hd (hd[t] = row j0 - t); the
+  // window holds rows j0-NB-Sb+1..j0-NB. Rows >= n are virtual: zero values, zero factor
+  // columns, zero 1/u_jj. x_head = inv(U_block) h_head, then every window row applies the
+  // panel's NB columns; the window's first NB rows move to hd. Two barriers per panel.
   auto issue_bwd = [&](int64_t Bp, int st) {
     unsigned char* dst = stage0 + (size_t)st * stage_bytes;
     const uint32_t bar = smem_u32(&mbar[st]);
@@ -260,16 +274,21 @@ __global__ void __maxnreg__(REGS) band_solve_kernel(SolveArgsT<CT> a) {
     bulk_g2s(smem_u32(dst + bwd_cols_bytes), Uip + (cb0 / NB) * 64, (uint32_t)(64 * sizeof(CT)),
              bar);
   };
-  const int Sb = kv + NB;
+  const int Sb = kv > NB ? kv : NB;
   int64_t row[SPT];
-  if (tid == 0)
+  if (tid == issuer)
     for (int st = 0; st < a.nstage && st < npanel; ++st) issue_bwd(st, st);
   {
     const int64_t j0 = a.n_pad - 1;
+    for (int e = tid; e < NB * NC; e += T) {
+      const int t = e / NC, c = e - (e / NC) * NC;
+      const int64_t r = j0 - t;
+      hd[e] = (r < n && c < ncol) ? Yo[(int64_t)(c0 + c) * a.ldy + r] : zero;
+    }
 #pragma unroll
     for (int u = 0; u < SPT; ++u) {
       const int s = tid + u * T;
-      const int64_t r = j0 - (((j0 - s) % Sb) + Sb) % Sb;
+      const int64_t r = j0 - NB - s;
       row[u] = r;
 #pragma unroll
       for (int c = 0; c < NC; ++c) {
@@ -278,9 +297,6 @@ __global__ void __maxnreg__(REGS) band_solve_kernel(SolveArgsT<CT> a) {
         nxt[u][c] = (s < Sb && rn >= 0 && rn < n && c < ncol) ? Yo[(int64_t)(c0 + c) * a.ldy + rn]
                                                              : zero;
       }
-      if (s < Sb && r > j0 - NB)
-#pragma unroll
-        for (int c = 0; c < NC; ++c) hd[(int)(j0 - r) * NC + c] = v[u][c];
     }
   }
   for (int64_t Bp = 0; Bp < npanel && !failed; ++Bp) {
@@ -289,13 +305,14 @@ __global__ void __maxnreg__(REGS) band_solve_kernel(SolveArgsT<CT> a) {
     __syncthreads();
     if (s_fail) { failed = true; break; }
     // the previous panel's stage is free: refill it
-    if (tid == 0 && Bp >= 1 && Bp - 1 + a.nstage < npanel)
+    if (tid == issuer && Bp >= 1 && Bp - 1 + a.nstage < npanel)
       issue_bwd(Bp - 1 + a.nstage, (int)((Bp - 1) % a.nstage));
     const CT* Ust = (const CT*)(stage0 + (size_t)st * stage_bytes);
     const CT* Uist = (const CT*)(stage0 + (size_t)st * stage_bytes + bwd_cols_bytes);
     const int64_t j0 = a.n_pad - 1 - Bp * NB;
     // head rows j0 - t (t = 0..NB-1) = block rows NB-1-t; matrix column j0 - s2 is stage
-    // column NB-1-s2. x_head = inv(U_block) h_head, one (row, column) per thread.
+    // column NB-1-s2. x_head = inv(U_block) h_head, one (row, column) per thread; the head
+    // rows leave with x
     for (int e = tid; e < NB * NC; e += T) {
       const int t = e / NC, c = e - (e / NC) * NC;
       CT acc = zero;
@@ -303,61 +320,45 @@ __global__ void __maxnreg__(REGS) band_solve_kernel(SolveArgsT<CT> a) {
       for (int t2 = 0; t2 < NB; ++t2)
         acc = cfma(Uist[(NB - 1 - t) * NB + (NB - 1 - t2)], hd[t2 * NC + c], acc);
       xs[t * NC + c] = acc;
+      const int64_t r = j0 - t;
+      if (r < n && c < ncol) {
+        if constexpr (sizeof(CT) == sizeof(cplx)) {
+          if (a.mode == 0) Yo[(int64_t)(c0 + c) * a.ldy + r] = cmul(w, acc);
+        }
+        if (a.mode == 1) Xo[(int64_t)(c0 + c) * a.ldx + r] = to_d(acc);
+        else if (a.mode == 3) Yo[(int64_t)(c0 + c) * a.ldy + r] = acc;   // y of row r is read
+      }
     }
     __syncthreads();
 #pragma unroll
     for (int u = 0; u < SPT; ++u) {
       const int s = tid + u * T;
       if (s >= Sb) continue;
-      int64_t r = row[u];
-      if (r > j0 - NB) {
-        const int t = (int)(j0 - r);
-        if (r < n) {
+      const int64_t r = row[u];
+      // d = (j0 - s2) - r in [1, kv] selects the band entries of this row
+      const int base = (int)(j0 - r);            // >= NB for every window row
 #pragma unroll
-          for (int c = 0; c < NC; ++c) {
-            if (c >= ncol) continue;
-            const CT xv = xs[t * NC + c];
-            if constexpr (sizeof(CT) == sizeof(cplx)) {
-              if (a.mode == 0) {
-                Yo[(int64_t)(c0 + c) * a.ldy + r] = cmul(w, xv);
-                continue;
-              }
-            }
-            if (a.mode == 1) {
-              Xo[(int64_t)(c0 + c) * a.ldx + r] = to_d(xv);
-            } else if (a.mode == 3) {
-              Yo[(int64_t)(c0 + c) * a.ldy + r] = xv;   // row r of y is no longer read
-            }
-          }
+      for (int s2 = 0; s2 < NB; ++s2) {
+        const int d = base - s2;
+        if (d <= kv) {
+          const CT uu = Ust[(size_t)(NB - 1 - s2) * kvp + kv - d];
+#pragma unroll
+          for (int c = 0; c < NC; ++c) v[u][c] = cfms(uu, xs[s2 * NC + c], v[u][c]);
         }
-        r -= Sb;
-        row[u] = r;
+      }
+      // rows j0-NB..j0-2NB+1 are the next panel's head: to hd, and the slot takes row r - Sb
+      const int dh = base - NB;
+      if (dh < NB) {
+#pragma unroll
+        for (int c = 0; c < NC; ++c) hd[dh * NC + c] = v[u][c];
+        const int64_t r2 = r - Sb;
+        row[u] = r2;
 #pragma unroll
         for (int c = 0; c < NC; ++c) {
           v[u][c] = nxt[u][c];
-          const int64_t rn = r - Sb;
-          nxt[u][c] = (rn >= 0 && c < ncol) ? Yo[(int64_t)(c0 + c) * a.ldy + rn] : zero;
+          const int64_t rn = r2 - Sb;
+          nxt[u][c] = (rn >= 0 && rn < n && c < ncol) ? Yo[(int64_t)(c0 + c) * a.ldy + rn] : zero;
         }
-        // a refilled row lies below every column of this block's band: no update; with
-        // kv < NB it can already be a head row of the next block
-        if (r > j0 - 2 * NB)
-#pragma unroll
-          for (int c = 0; c < NC; ++c) hd[(int)(j0 - NB - r) * NC + c] = v[u][c];
-      } else {
-        // d = (j0 - s2) - r in [1, kv] selects the band entries of this row
-        const int base = (int)(j0 - r);
-#pragma unroll
-        for (int s2 = 0; s2 < NB; ++s2) {
-          const int d = base - s2;
-          if (d >= 1 && d <= kv) {
-            const CT uu = Ust[(size_t)(NB - 1 - s2) * kvp + kv - d];
-#pragma unroll
-            for (int c = 0; c < NC; ++c) v[u][c] = cfms(uu, xs[s2 * NC + c], v[u][c]);
-          }
-        }
-        if (r > j0 - 2 * NB)
-#pragma unroll
-          for (int c = 0; c < NC; ++c) hd[(int)(j0 - NB - r) * NC + c] = v[u][c];
       }
     }
   }
@@ -378,17 +379,26 @@ __global__ void __maxnreg__(REGS) band_solve_kernel(SolveArgsT<CT> a) {
 //  backward: inv(U_block), the 8x8 inverse of U's diagonal block of the panel (rows and
 //    columns >= n are zero).
 // T and inv(U_block) are written in complex128 and, when T32/Ui32 are given, complex64.
-__global__ void block_transform_kernel(int64_t n, int64_t n_pad, int kl, int ldab, const cplx* AB,
-                                       const int* piv, const cplx* dinv, cplx* Tout, int* Hout,
+__device__ __forceinline__ cplx ld_c(const cplx* p) { return *p; }
+__device__ __forceinline__ cplx ld_c(const float2* p) {
+  const float2 v = *p;
+  return make_double2(v.x, v.y);
+}
+
+// AT: element type of the band factors and 1/u_jj (complex128, or complex64 from the FP32 LU;
+// the transforms are then formed in FP64 from the complex64 entries and rounded).
+template <typename AT>
+__global__ void block_transform_kernel(int64_t n, int64_t n_pad, int kl, int ldab, const AT* AB,
+                                       const int* piv, const AT* dinv, cplx* Tout, int* Hout,
                                        cplx* Uiout, float2* T32, float2* Ui32) {
   const int P = blockIdx.x, pole = blockIdx.y, lane = threadIdx.x;
   const int kv = 2 * kl;
   const int64_t npan = n_pad / NB;
   const int64_t j0 = (int64_t)P * NB;
   const int nvalid = (int)((n - j0) < NB ? (n - j0) : NB);
-  const cplx* A = AB + (int64_t)pole * n_pad * ldab;
+  const AT* A = AB + (int64_t)pole * n_pad * ldab;
   const int* pv = piv + (int64_t)pole * n_pad;
-  const cplx* di = dinv + (int64_t)pole * n_pad;
+  const AT* di = dinv + (int64_t)pole * n_pad;
   int64_t pst[NB];
 #pragma unroll
   for (int jj = 0; jj < NB; ++jj) pst[jj] = (jj < nvalid) ? pv[j0 + jj] : -1;
@@ -421,12 +431,12 @@ __global__ void block_transform_kernel(int64_t n, int64_t n_pad, int kl, int lda
                                      __shfl_sync(0xffffffffu, val.y, jj));
         if (lane == jj) val = x;
         else if (lane == b) val = va;
-        if (myrow > j && myrow <= j + kl) val = cfms(A[j * ldab + kv + (myrow - j)], x, val);
+        if (myrow > j && myrow <= j + kl) val = cfms(ld_c(A + j * ldab + kv + (myrow - j)), x, val);
       }
     }
     if (lane < 16) {
       const cplx t = (myrow >= 0 && present) ? val : make_double2(0, 0);
-      Tout[base * 256 + lane * 16 + m] = t;
+      if (Tout) Tout[base * 256 + lane * 16 + m] = t;
       if (T32) T32[base * 256 + lane * 16 + m] = make_float2((float)t.x, (float)t.y);
     }
   }
@@ -440,12 +450,12 @@ __global__ void block_transform_kernel(int64_t n, int64_t n_pad, int kl, int lda
       const int64_t r = j0 + i;
       cplx acc = make_double2(i == b ? 1.0 : 0.0, 0.0);
       for (int c = i + 1; c <= b; ++c)
-        if (c - i <= kv && j0 + c < n) acc = cfms(A[(j0 + c) * ldab + kv + (r - (j0 + c))], z[c], acc);
-      z[i] = (r < n) ? cmul(acc, di[r]) : make_double2(0, 0);
+        if (c - i <= kv && j0 + c < n) acc = cfms(ld_c(A + (j0 + c) * ldab + kv + (r - (j0 + c))), z[c], acc);
+      z[i] = (r < n) ? cmul(acc, ld_c(di + r)) : make_double2(0, 0);
     }
     for (int i = 0; i < NB; ++i) {
       const cplx t = z[i];
-      Uiout[base * 64 + i * NB + b] = t;
+      if (Uiout) Uiout[base * 64 + i * NB + b] = t;
       if (Ui32) Ui32[base * 64 + i * NB + b] = make_float2((float)t.x, (float)t.y);
     }
   }
@@ -455,7 +465,14 @@ void launch_block_transforms(int q, int64_t n, int64_t n_pad, int kl, int ldab, 
                              const int* piv, const cplx* dinv, cplx* T, int* H, cplx* Ui,
                              float2* T32, float2* Ui32, cudaStream_t s) {
   dim3 grid((unsigned)(n_pad / NB), (unsigned)q);
-  block_transform_kernel<<<grid, 32, 0, s>>>(n, n_pad, kl, ldab, AB, piv, dinv, T, H, Ui, T32, Ui32); ie_count_launch();
+  block_transform_kernel<cplx><<<grid, 32, 0, s>>>(n, n_pad, kl, ldab, AB, piv, dinv, T, H, Ui, T32, Ui32); ie_count_launch();
+}
+
+void launch_block_transforms(int q, int64_t n, int64_t n_pad, int kl, int ldab, const float2* AB,
+                             const int* piv, const float2* dinv, int* H, float2* T32,
+                             float2* Ui32, cudaStream_t s) {
+  dim3 grid((unsigned)(n_pad / NB), (unsigned)q);
+  block_transform_kernel<float2><<<grid, 32, 0, s>>>(n, n_pad, kl, ldab, AB, piv, dinv, nullptr, H, nullptr, T32, Ui32); ie_count_launch();
 }
 
 template <typename CT, int NC, int SPT, int REGS>
@@ -489,14 +506,14 @@ struct SolveCfg {
 // threads, stages and dynamic shared memory of a shape; false if the shape cannot hold the band
 template <typename CT>
 static bool shape_for(SolveArgsT<CT>& a, const SolveCfg& c, int* threads, size_t* smem) {
-  const int slots = a.kv + NB;                  // backward window (larger than kl + NB)
+  const int slots = a.kv > NB ? a.kv : NB;     // backward window (at least the forward's)
   if ((slots + c.spt - 1) / c.spt > 576) return false;
   *threads = ((slots + c.spt - 1) / c.spt + 31) / 32 * 32;
   const size_t fwdb = (size_t)NB * a.klp * sizeof(CT) + 256 * sizeof(CT) + 16 * sizeof(int);
   const size_t bwdb = (size_t)NB * a.kvp * sizeof(CT) + 64 * sizeof(CT);
   const size_t stage_bytes = ((fwdb > bwdb ? fwdb : bwdb) + 127) & ~(size_t)127;
-  // mbarriers, then bc [4][NC], hd and xs [NB][NC], hv and hv2 [16][NC], alignment slack
-  const size_t fixed = 128 + (size_t)(4 + 2 * NB + 32) * c.nc * sizeof(CT) + 256;
+  // mbarriers, then hd and xs [NB][NC], hv and hv2 [16][NC], alignment slack
+  const size_t fixed = 128 + (size_t)(2 * NB + 32) * c.nc * sizeof(CT) + 256;
   const size_t budget = 200 * 1024;
   if (fixed + 2 * stage_bytes > budget) return false;
   int nstage = (int)((budget - fixed) / stage_bytes);
@@ -572,7 +589,7 @@ static cudaError_t launch_tuned(const SolveArgsT<CT>& a, int q, cudaStream_t s) 
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const bool fp32 = sizeof(CT) == sizeof(float2);
-  const int spt0 = (a.kv + NB > 576) ? 2 : 1;
+  const int spt0 = ((a.kv > NB ? a.kv : NB) > 576) ? 2 : 1;
   const SolveCfg dflt{pick_nc(q, a.k, sms, fp32 ? 8 : 4), spt0, 6};
   if (!tune_enabled()) return launch_cfg(a, q, dflt, s);
   int kb = 1;

@@ -60,7 +60,7 @@ def test_apply_GH_ragged_ld_and_host_buffers(ie):
         Gd = torch.zeros((k, c.n + 5), dtype=torch.complex128, device="cuda:0")
         assert ie.ie_apply_GH(c.h, Vd.T[: c.n], Gd.T[: c.n]) == ie.IE_OK   # ld = n + 3, n + 5
         Gh = np.zeros((c.n, k), dtype=np.complex128, order="F")
-        assert ie.ie_apply_GH(c.h, Vpad, Gh) == ie.IE_OK
+        assert ie.ie_apply_GH(c.h, Vpad[: c.n], Gh) == ie.IE_OK              # host, ld = n + 3
         ref = oadj.adjoint_inner(c.A, c.B, c.w["center"], c.w["radius"], c.w["q"]).apply(V)
         for got in (Gd.T.cpu().numpy()[: c.n], Gh):
             assert np.linalg.norm(got - ref) / np.linalg.norm(ref) < 1e-11

@@ -5,7 +5,7 @@ import numpy as np
 import pytest
 
 import ie_inputs
-from oracle import inner, msgmres
+from oracle import coeffs, inner, msgmres
 
 from test_gpu_parity import Case, colerr, dblock, dzeros, golden_eigs, match_eigs
 
@@ -83,13 +83,47 @@ def test_mixed_solve_matches_golden(ie, name, driver):
 
 
 def test_mixed_handle_has_no_complex128_factors(ie):
-    """A precision = 1 handle releases its complex128 factors: the entry points that read
-    them refuse it instead of touching released memory."""
+    """A precision = 1 handle has complex64 factors only: the complex128 static G path
+    refuses it instead of touching factors it does not have."""
     c = mixed(ie, "c1_m24")
     try:
-        st, ab, ipiv, kl = ie.ie_get_factor(c.h, 0, c.n, 3 * c.pen.half_bw + 1)
-        assert st == ie.IE_ERR_ARG
         V = dblock(ie_inputs.random_block(c.n, 2, seed=1))
         assert ie.ie_apply_G_static(c.h, V, dzeros(c.n, 2)) == ie.IE_ERR_ARG
+    finally:
+        c.close()
+
+
+@pytest.mark.parametrize("name", ["c1_m24", "r1_m37"])
+def test_mixed_lu_is_cgbtrf(ie, name):
+    """The mixed handle factors K_i = p_i B - A, assembled in complex64, by the band LU in FP32
+    arithmetic (LAPACK cgbtf2 semantics: pivot = first max of |re| + |im|). Against LAPACK's
+    cgbtrf on the same complex64 band: the same pivot rows (the two round the rank-1 updates
+    in different orders, so a near-tie could flip one; none does on these pencils), factors
+    equal to FP32 rounding, and the factors solve K x = b to an FP32-level backward error."""
+    from scipy.linalg import lapack
+    c = mixed(ie, name)
+    try:
+        n, m = c.n, c.pen.half_bw
+        ldab = 3 * m + 1
+        poles, _ = coeffs.trapezoid_poles_weights(c.w["center"], c.w["radius"], c.w["q"])
+        for i, pole in enumerate(poles):
+            st, ab, ipiv, kl = ie.ie_get_factor(c.h, i, n, ldab)
+            assert st == ie.IE_OK and kl == m
+            K = (pole * c.B - c.A).toarray()
+            K32 = K.astype(np.complex64)
+            band = np.zeros((ldab, n), dtype=np.complex64, order="F")
+            for j in range(n):
+                for r in range(max(0, j - m), min(n, j + m + 1)):
+                    band[2 * m + r - j, j] = K32[r, j]
+            lu, piv_ref, info = lapack.cgbtrf(band, m, m)
+            assert info == 0
+            assert np.array_equal(ipiv, piv_ref + 1), "pivot rows differ from cgbtrf"
+            scale = np.abs(lu).max()
+            assert np.max(np.abs(ab - lu)) <= 1e-4 * scale
+            b = ie_inputs.random_block(n, 2, seed=i)
+            x, info = lapack.zgbtrs(ab, m, m, b, ipiv - 1)
+            assert info == 0
+            res = np.linalg.norm(K @ x - b) / (np.linalg.norm(K, 1) * np.linalg.norm(x))
+            assert res < 1e-5, res
     finally:
         c.close()
