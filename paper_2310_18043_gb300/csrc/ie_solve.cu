@@ -371,6 +371,417 @@ __global__ void __maxnreg__(REGS) band_solve_kernel(SolveArgsT<CT> a) {
 }
 
 // ----------------------------------------------------------------------------------------------
+// Warp-specialised form of the same solve: no CTA-wide barrier per panel.
+//
+// Roles: warps 0..WU-1 hold the register window (as above, slot = tid + u*WU*32); warp WU is
+// the head warp (the forward H <- T H and the backward x_head = inv(U_block) h_head, and the
+// head rows' global outputs); warp WU+1 is the producer (bulk copies of the factor panels).
+// The two sweeps are one sequence of 2*npanel panels G (forward P = G, backward Bp =
+// G - npanel) sharing a ring of ns stages. Stage G % ns holds the factor panel (bulk copy),
+// the head warp's output OUT (forward: T H, 16 x NC; backward: x_head, NB x NC) and its input
+// IN (forward: the 16 members; backward: the NB head rows). Per stage four mbarriers:
+//   FULL  (bulk copy landed; count 1 + tx bytes),
+//   EMPTY (every update warp and the head warp are done with the stage; count WU + 1),
+//   HDF   (IN complete; count 2*NB: one arrival per head row from the update thread that holds
+//          it, one per present pivot member (forward), the rest by the head warp),
+//   XSF   (OUT complete; count 1, the head warp).
+// An update thread whose row becomes a head row of panel G+1 writes it into IN(G+1) and
+// arrives on HDF(G+1) as soon as its own update of panel G is done, so the head warp starts
+// panel G+1 while other rows are still being updated with panel G. Every barrier of panel G
+// waits behind FULL(G), and FULL(G) behind EMPTY(G - ns), so no warp runs ns panels ahead of
+// another and no mbarrier phase is passed twice unseen. The in-place output of the backward
+// sweep (mode 0/3) is safe: a row's y is loaded by the thread that later hands the row to
+// the head warp. Every wait is bounded; on a timeout the CTA records ST_TIMEOUT, every warp
+// leaves its loop, and the producer waits for the bulk copies it issued before exiting.
+namespace {
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_cnt(uint32_t bar, uint32_t cnt) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(cnt) : "memory");
+}
+// bounded wait that also gives up when another warp has recorded a failure; a timeout is
+// recorded in the CTA's flag and in the kernel's status word
+__device__ __forceinline__ bool pwait(uint32_t bar, uint32_t parity, volatile int* fail,
+                                      int* status) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const unsigned long long t0 = ie_globaltimer();
+  while (true) {
+    for (int i = 0; i < 32; ++i)
+      if (mbar_try_wait(bar, parity)) return true;
+    if (*fail) return false;
+    if (ie_globaltimer() - t0 > IE_WAIT_NS) {
+      *fail = 1;
+      atomicExch(status + ST_TIMEOUT, 1);
+      return false;
+    }
+  }
+}
+}  // namespace
+
+template <typename CT, int NC, int SPT, int REGS>
+__global__ void __maxnreg__(REGS) band_solve_pipe_kernel(SolveArgsT<CT> a) {
+  const int pole = blockIdx.y;
+  const int c0 = blockIdx.x * NC;
+  const int ncol = min(NC, a.k - c0);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int WU = (int)(blockDim.x >> 5) - 2;      // update warps
+  const int TU = WU * 32;                         // update threads
+  const int kl = a.kl, kv = a.kv, klp = a.klp, kvp = a.kvp;
+  const int64_t n = a.n;
+  const CT* Lp = a.L + (int64_t)pole * a.lstride;
+  const CT* Up = a.U + (int64_t)pole * a.ustride;
+  const int64_t npan = a.n_pad / NB;
+  const CT* Tp = a.Tb + (int64_t)pole * npan * 256;
+  const int* Hp = a.Hb + (int64_t)pole * npan * 16;
+  const CT* Uip = a.Ub + (int64_t)pole * npan * 64;
+  const CT* R = a.RHS + (int64_t)pole * a.rstride;
+  CT* Yo = a.Y + (int64_t)pole * a.ystride;
+  cplx* Xo = a.X + (int64_t)pole * a.xstride;
+  const cplx w = a.weights[pole];
+  const CT zero{};
+  const int ns = a.nstage;
+  const int64_t npanel = npan, total = 2 * npan;
+
+  extern __shared__ __align__(128) unsigned char sm_raw[];
+  uint64_t* bars = (uint64_t*)sm_raw;             // [4][ns]: FULL, EMPTY, HDF, XSF
+  const size_t fwd_cols_bytes = (size_t)NB * klp * sizeof(CT);
+  const size_t bwd_cols_bytes = (size_t)NB * kvp * sizeof(CT);
+  const size_t fwd_bytes = fwd_cols_bytes + 256 * sizeof(CT) + 16 * sizeof(int);
+  const size_t bwd_bytes = bwd_cols_bytes + 64 * sizeof(CT);
+  const size_t fac_bytes = ((fwd_bytes > bwd_bytes ? fwd_bytes : bwd_bytes) + 127) & ~(size_t)127;
+  const size_t io_bytes = (size_t)16 * NC * sizeof(CT);
+  const size_t stage_bytes = (fac_bytes + 2 * io_bytes + 127) & ~(size_t)127;
+  unsigned char* stage0 = sm_raw + ((4 * (size_t)ns * 8 + 127) & ~(size_t)127);
+  __shared__ int s_fail_raw;
+  volatile int* s_fail = &s_fail_raw;
+  {
+    unsigned dsz;
+    asm("mov.u32 %0, %%dynamic_smem_size;" : "=r"(dsz));
+    if ((size_t)(stage0 - sm_raw) + (size_t)ns * stage_bytes > (size_t)dsz || WU < 1) {
+      if (tid == 0) atomicExch(a.status + ST_TIMEOUT, 1);
+      return;
+    }
+  }
+  auto FULL = [&](int64_t G) { return smem_u32(&bars[0 * ns + (int)(G % ns)]); };
+  auto EMPTY = [&](int64_t G) { return smem_u32(&bars[1 * ns + (int)(G % ns)]); };
+  auto HDF = [&](int64_t G) { return smem_u32(&bars[2 * ns + (int)(G % ns)]); };
+  auto XSF = [&](int64_t G) { return smem_u32(&bars[3 * ns + (int)(G % ns)]); };
+  auto par = [&](int64_t G) { return (uint32_t)((G / ns) & 1); };
+  auto FAC = [&](int64_t G) { return stage0 + (size_t)(G % ns) * stage_bytes; };
+  auto OUT = [&](int64_t G) { return (CT*)(stage0 + (size_t)(G % ns) * stage_bytes + fac_bytes); };
+  auto IN = [&](int64_t G) {
+    return (CT*)(stage0 + (size_t)(G % ns) * stage_bytes + fac_bytes + io_bytes);
+  };
+  if (tid == 0) {
+    s_fail_raw = 0;
+    for (int i = 0; i < ns; ++i) {
+      mbar_init(smem_u32(&bars[0 * ns + i]), 1);
+      mbar_init(smem_u32(&bars[1 * ns + i]), (uint32_t)(WU + 1));
+      mbar_init(smem_u32(&bars[2 * ns + i]), 2 * NB);
+      mbar_init(smem_u32(&bars[3 * ns + i]), 1);
+    }
+    mbar_fence_init();
+  }
+  __syncthreads();
+
+  const int Sf = kl > NB ? kl : NB;
+  const int Sb = kv > NB ? kv : NB;
+  // ---------------------------------------------------------------- producer warp
+  auto issue = [&](int64_t G) {
+    unsigned char* dst = FAC(G);
+    const uint32_t bar = FULL(G);
+    if (G < npanel) {
+      const int64_t P = G;
+      mbar_expect_tx(bar, (uint32_t)fwd_bytes);
+      bulk_g2s(smem_u32(dst), Lp + P * NB * a.ldl, (uint32_t)fwd_cols_bytes, bar);
+      bulk_g2s(smem_u32(dst + fwd_cols_bytes), Tp + P * 256, (uint32_t)(256 * sizeof(CT)), bar);
+      bulk_g2s(smem_u32(dst + fwd_cols_bytes + 256 * sizeof(CT)), Hp + P * 16,
+               (uint32_t)(16 * sizeof(int)), bar);
+    } else {
+      const int64_t cb0 = a.n_pad - (G - npanel + 1) * NB;
+      mbar_expect_tx(bar, (uint32_t)bwd_bytes);
+      bulk_g2s(smem_u32(dst), Up + cb0 * a.ldu, (uint32_t)bwd_cols_bytes, bar);
+      bulk_g2s(smem_u32(dst + bwd_cols_bytes), Uip + (cb0 / NB) * 64, (uint32_t)(64 * sizeof(CT)),
+               bar);
+    }
+  };
+  int64_t issued = 0;
+  auto produce_until = [&](int64_t Gend) {   // lane 0 of the producer warp
+    for (; issued < Gend && !*s_fail; ++issued) {
+      if (issued >= ns && !pwait(EMPTY(issued - ns), par(issued - ns), s_fail, a.status)) break;
+      issue(issued);
+    }
+  };
+  auto drain = [&]() {   // wait for the bulk copies still in flight (bounded)
+    for (int64_t G = issued - ns > 0 ? issued - ns : 0; G < issued; ++G)
+      if (!mbar_wait_bounded(FULL(G), par(G))) atomicExch(a.status + ST_TIMEOUT, 1);
+  };
+  const bool is_prod = warp == WU + 1, is_head = warp == WU;
+
+  // ---------------------------------------------------------------- forward sweep
+  CT v[SPT][NC], nxt[SPT][NC];
+  int64_t frow[SPT];
+  int mem[SPT];
+  if (is_prod) {
+    if (lane == 0) {
+      produce_until(npanel + ns < total ? npanel + ns : total);
+      if (*s_fail) drain();
+    }
+  } else if (is_head) {
+    // panel 0's head rows come from the right-hand side; the head warp also completes the
+    // HDF count of every forward panel for the pivot members that are absent
+    for (int e = lane; e < NB * NC; e += 32) {
+      const int t = e / NC, c = e - (e / NC) * NC;
+      IN(0)[t * NC + c] = (t < n && c < ncol) ? R[(int64_t)(c0 + c) * a.ldr + t] : zero;
+    }
+    __syncwarp();
+    if (lane == 0) mbar_arrive_cnt(HDF(0), NB);
+    for (int64_t P = 0; P < npanel; ++P) {
+      const int64_t G = P;
+      if (!pwait(FULL(G), par(G), s_fail, a.status)) break;
+      const unsigned char* st = FAC(G);
+      const CT* Tst = (const CT*)(st + fwd_cols_bytes);
+      const int* Hst = (const int*)(st + fwd_cols_bytes + 256 * sizeof(CT));
+      int npres = 0;
+#pragma unroll
+      for (int i = NB; i < 16; ++i) npres += Hst[i] >= 0;
+      if (lane == 0 && npres < NB) mbar_arrive_cnt(HDF(G), (uint32_t)(NB - npres));
+      if (!pwait(HDF(G), par(G), s_fail, a.status)) break;
+      const CT* hv = IN(G);
+      CT* hv2 = OUT(G);
+      const int64_t j0 = P * NB;
+      const int nvalid = (int)((n - j0) < NB ? (n - j0) : NB);
+      for (int e = lane; e < 16 * NC; e += 32) {
+        const int i = e / NC, c = e - (e / NC) * NC;
+        if (Hst[i] >= 0) {
+          CT acc = zero;
+#pragma unroll 4
+          for (int m = 0; m < 16; ++m)
+            if (Hst[m] >= 0) acc = cfma(Tst[i * 16 + m], hv[m * NC + c], acc);
+          hv2[i * NC + c] = acc;
+          if (i < nvalid && c < ncol) Yo[(int64_t)(c0 + c) * a.ldy + j0 + i] = acc;
+        }
+      }
+      __syncwarp();
+      if (lane == 0) {
+        mbar_arrive(XSF(G));
+        mbar_arrive(EMPTY(G));
+      }
+    }
+  } else {
+    // update warps: initial window rows NB.. and panel 0's pivot members
+#pragma unroll
+    for (int u = 0; u < SPT; ++u) {
+      const int s = tid + u * TU;
+      const int64_t r = NB + s;
+      frow[u] = r;
+#pragma unroll
+      for (int c = 0; c < NC; ++c) {
+        v[u][c] = (s < Sf && r < n && c < ncol) ? R[(int64_t)(c0 + c) * a.ldr + r] : zero;
+        nxt[u][c] = (s < Sf && r + Sf < n && c < ncol) ? R[(int64_t)(c0 + c) * a.ldr + r + Sf] : zero;
+      }
+    }
+    // member index of each slot for panel P (H entries NB..15), and hand the members over
+    auto members = [&](int64_t P) -> bool {
+      const int64_t G = P;
+      if (!pwait(FULL(G), par(G), s_fail, a.status)) return false;
+      const int* Hst = (const int*)(FAC(G) + fwd_cols_bytes + 256 * sizeof(CT));
+      CT* hv = IN(G);
+      const int j0i = (int)(P * NB);
+#pragma unroll
+      for (int u = 0; u < SPT; ++u) {
+        const int s = tid + u * TU;
+        mem[u] = -1;
+        if (s >= Sf) continue;
+        const int dr = (int)(frow[u] - P * NB);
+#pragma unroll
+        for (int i = NB; i < 16; ++i)
+          if (Hst[i] - j0i == dr) mem[u] = i;
+        if (mem[u] >= 0) {
+#pragma unroll
+          for (int c = 0; c < NC; ++c) hv[mem[u] * NC + c] = v[u][c];
+          mbar_arrive(HDF(G));
+        }
+      }
+      return true;
+    };
+    bool ok = members(0);
+    for (int64_t P = 0; P < npanel && ok; ++P) {
+      const int64_t G = P;
+      if (!pwait(XSF(G), par(G), s_fail, a.status)) break;   // FULL(G) was waited on by members(P)
+      const unsigned char* st = FAC(G);
+      const CT* Lst = (const CT*)st;
+      const CT* hv2 = OUT(G);
+      const int64_t j0 = P * NB;
+      const int nvalid = (int)((n - j0) < NB ? (n - j0) : NB);
+      const bool more = P + 1 < npanel;
+      CT* hdn = more ? IN(G + 1) : nullptr;
+#pragma unroll
+      for (int u = 0; u < SPT; ++u) {
+        const int s = tid + u * TU;
+        if (s >= Sf) continue;
+        const int64_t r = frow[u];
+        const int i = mem[u];
+        if (i >= NB) {
+#pragma unroll
+          for (int c = 0; c < NC; ++c) v[u][c] = hv2[i * NC + c];
+        } else {
+          const int dr = (int)(r - j0);
+#pragma unroll
+          for (int jj = 0; jj < NB; ++jj) {
+            const int dd = dr - jj;
+            if (jj < nvalid && dd <= kl) {
+              const CT lv = Lst[jj * klp + dd - 1];
+#pragma unroll
+              for (int c = 0; c < NC; ++c) v[u][c] = cfms(lv, hv2[jj * NC + c], v[u][c]);
+            }
+          }
+        }
+        const int dh = (int)(r - j0) - NB;
+        if (dh < NB) {   // a head row of panel P+1: hand it over, take row r + Sf
+          if (more) {
+#pragma unroll
+            for (int c = 0; c < NC; ++c) hdn[dh * NC + c] = v[u][c];
+            mbar_arrive(HDF(G + 1));
+          }
+          const int64_t r2 = r + Sf;
+          frow[u] = r2;
+#pragma unroll
+          for (int c = 0; c < NC; ++c) {
+            v[u][c] = nxt[u][c];
+            nxt[u][c] = (r2 + Sf < n && c < ncol) ? R[(int64_t)(c0 + c) * a.ldr + r2 + Sf] : zero;
+          }
+        }
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(EMPTY(G));
+      if (more && !members(P + 1)) break;
+    }
+  }
+  // the forward results y (written by the head warp) are read back by every warp below
+  __syncthreads();
+
+  // ---------------------------------------------------------------- backward sweep
+  if (!*s_fail) {
+    if (is_prod) {
+      if (lane == 0) {
+        produce_until(total);
+        // stay until every stage has been consumed, so that no bulk copy can outlive the CTA
+        for (int64_t G = total - ns > 0 ? total - ns : 0; G < total && !*s_fail; ++G)
+          pwait(EMPTY(G), par(G), s_fail, a.status);
+        if (*s_fail) drain();
+      }
+    } else if (is_head) {
+      {
+        const int64_t j0 = a.n_pad - 1;
+        CT* hd = IN(npanel);
+        for (int e = lane; e < NB * NC; e += 32) {
+          const int t = e / NC, c = e - (e / NC) * NC;
+          const int64_t r = j0 - t;
+          hd[e] = (r < n && c < ncol) ? Yo[(int64_t)(c0 + c) * a.ldy + r] : zero;
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive_cnt(HDF(npanel), NB);
+      }
+      for (int64_t Bp = 0; Bp < npanel; ++Bp) {
+        const int64_t G = npanel + Bp;
+        if (!pwait(FULL(G), par(G), s_fail, a.status)) break;
+        if (lane == 0) mbar_arrive_cnt(HDF(G), NB);
+        if (!pwait(HDF(G), par(G), s_fail, a.status)) break;
+        const CT* Uist = (const CT*)(FAC(G) + bwd_cols_bytes);
+        const CT* hd = IN(G);
+        CT* xs = OUT(G);
+        const int64_t j0 = a.n_pad - 1 - Bp * NB;
+        for (int e = lane; e < NB * NC; e += 32) {
+          const int t = e / NC, c = e - (e / NC) * NC;
+          CT acc = zero;
+#pragma unroll
+          for (int t2 = 0; t2 < NB; ++t2)
+            acc = cfma(Uist[(NB - 1 - t) * NB + (NB - 1 - t2)], hd[t2 * NC + c], acc);
+          xs[t * NC + c] = acc;
+          const int64_t r = j0 - t;
+          if (r < n && c < ncol) {
+            if constexpr (sizeof(CT) == sizeof(cplx)) {
+              if (a.mode == 0) Yo[(int64_t)(c0 + c) * a.ldy + r] = cmul(w, acc);
+            }
+            if (a.mode == 1) Xo[(int64_t)(c0 + c) * a.ldx + r] = to_d(acc);
+            else if (a.mode == 3) Yo[(int64_t)(c0 + c) * a.ldy + r] = acc;
+          }
+        }
+        __syncwarp();
+        if (lane == 0) {
+          mbar_arrive(XSF(G));
+          mbar_arrive(EMPTY(G));
+        }
+      }
+    } else {
+      int64_t row[SPT];
+      {
+        const int64_t j0 = a.n_pad - 1;
+#pragma unroll
+        for (int u = 0; u < SPT; ++u) {
+          const int s = tid + u * TU;
+          const int64_t r = j0 - NB - s;
+          row[u] = r;
+#pragma unroll
+          for (int c = 0; c < NC; ++c) {
+            v[u][c] = (s < Sb && r >= 0 && r < n && c < ncol) ? Yo[(int64_t)(c0 + c) * a.ldy + r] : zero;
+            const int64_t rn = r - Sb;
+            nxt[u][c] = (s < Sb && rn >= 0 && rn < n && c < ncol) ? Yo[(int64_t)(c0 + c) * a.ldy + rn]
+                                                                 : zero;
+          }
+        }
+      }
+      for (int64_t Bp = 0; Bp < npanel; ++Bp) {
+        const int64_t G = npanel + Bp;
+        if (!pwait(FULL(G), par(G), s_fail, a.status)) break;
+        if (!pwait(XSF(G), par(G), s_fail, a.status)) break;
+        const CT* Ust = (const CT*)FAC(G);
+        const CT* xs = OUT(G);
+        const int64_t j0 = a.n_pad - 1 - Bp * NB;
+        const bool more = Bp + 1 < npanel;
+        CT* hdn = more ? IN(G + 1) : nullptr;
+#pragma unroll
+        for (int u = 0; u < SPT; ++u) {
+          const int s = tid + u * TU;
+          if (s >= Sb) continue;
+          const int64_t r = row[u];
+          const int base = (int)(j0 - r);
+#pragma unroll
+          for (int s2 = 0; s2 < NB; ++s2) {
+            const int d = base - s2;
+            if (d <= kv) {
+              const CT uu = Ust[(size_t)(NB - 1 - s2) * kvp + kv - d];
+#pragma unroll
+              for (int c = 0; c < NC; ++c) v[u][c] = cfms(uu, xs[s2 * NC + c], v[u][c]);
+            }
+          }
+          const int dh = base - NB;
+          if (dh < NB) {
+            if (more) {
+#pragma unroll
+              for (int c = 0; c < NC; ++c) hdn[dh * NC + c] = v[u][c];
+              mbar_arrive(HDF(G + 1));
+            }
+            const int64_t r2 = r - Sb;
+            row[u] = r2;
+#pragma unroll
+            for (int c = 0; c < NC; ++c) {
+              v[u][c] = nxt[u][c];
+              const int64_t rn = r2 - Sb;
+              nxt[u][c] = (rn >= 0 && rn < n && c < ncol) ? Yo[(int64_t)(c0 + c) * a.ldy + rn] : zero;
+            }
+          }
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(EMPTY(G));
+      }
+    }
+  }
+}
+
+// ----------------------------------------------------------------------------------------------
 // Block transforms, computed once per factorisation (one warp per (panel, pole)):
 //  forward: the set H of a panel's NB steps (head rows j0..j0+NB-1, then for step jj its pivot
 //    row if it lies below the head and no earlier step named it; -1 = absent) and the 16x16
@@ -497,16 +908,60 @@ static cudaError_t launch_solve_t(const SolveArgsT<CT>& a, int q, int threads, s
   return launch_solve_r<CT, NC, SPT, 96>(a, q, threads, smem, s);
 }
 
+template <typename CT, int NC, int SPT, int REGS>
+static cudaError_t launch_pipe_r(const SolveArgsT<CT>& a, int q, int threads, size_t smem,
+                                 cudaStream_t s) {
+  auto kfn = band_solve_pipe_kernel<CT, NC, SPT, REGS>;
+  cudaError_t e = ie_smem_optin((const void*)kfn);
+  if (e != cudaSuccess) return e;
+  int blocks = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, kfn, threads, smem);
+  if (e != cudaSuccess) return e;
+  if (blocks < 1) return cudaErrorLaunchOutOfResources;   // refuse rather than fail the launch
+  dim3 grid((unsigned)((a.k + NC - 1) / NC), (unsigned)q);
+  kfn<<<grid, threads, smem, s>>>(a); ie_count_launch();
+  return cudaGetLastError();
+}
+
+// register budget by warps per sub-partition: ceil(W/4) * 32 * REGS <= 16384
+template <typename CT, int NC, int SPT>
+static cudaError_t launch_pipe_t(const SolveArgsT<CT>& a, int q, int threads, size_t smem,
+                                 cudaStream_t s) {
+  const int wps = (threads / 32 + 3) / 4;
+  if (wps <= 4) return launch_pipe_r<CT, NC, SPT, 128>(a, q, threads, smem, s);
+  if (wps <= 5) return launch_pipe_r<CT, NC, SPT, 96>(a, q, threads, smem, s);
+  return cudaErrorInvalidValue;
+}
+
 // One launch shape: NC right-hand sides per CTA, SPT window slots per thread, at most
-// `stages` staged panels.
+// `stages` staged panels; pipe = 1 for the warp-specialised kernel.
 struct SolveCfg {
-  int nc, spt, stages;
+  int nc, spt, stages, pipe;
 };
 
 // threads, stages and dynamic shared memory of a shape; false if the shape cannot hold the band
 template <typename CT>
 static bool shape_for(SolveArgsT<CT>& a, const SolveCfg& c, int* threads, size_t* smem) {
   const int slots = a.kv > NB ? a.kv : NB;     // backward window (at least the forward's)
+  if (c.pipe) {
+    // update warps for the window, then the head warp and the producer warp
+    const int wu = ((slots + c.spt - 1) / c.spt + 31) / 32;
+    *threads = (wu + 2) * 32;
+    if (*threads > 640) return false;
+    const size_t fwdb = (size_t)NB * a.klp * sizeof(CT) + 256 * sizeof(CT) + 16 * sizeof(int);
+    const size_t bwdb = (size_t)NB * a.kvp * sizeof(CT) + 64 * sizeof(CT);
+    const size_t fac = ((fwdb > bwdb ? fwdb : bwdb) + 127) & ~(size_t)127;
+    const size_t stage_bytes = (fac + 2 * (size_t)16 * c.nc * sizeof(CT) + 127) & ~(size_t)127;
+    const size_t budget = 200 * 1024;
+    int nstage = c.stages;
+    while (nstage > 2 && ((4 * (size_t)nstage * 8 + 127) & ~(size_t)127) + nstage * stage_bytes > budget)
+      --nstage;
+    const size_t need = ((4 * (size_t)nstage * 8 + 127) & ~(size_t)127) + nstage * stage_bytes;
+    if (need > budget) return false;
+    a.nstage = nstage;
+    *smem = need;
+    return true;
+  }
   if ((slots + c.spt - 1) / c.spt > 576) return false;
   *threads = ((slots + c.spt - 1) / c.spt + 31) / 32 * 32;
   const size_t fwdb = (size_t)NB * a.klp * sizeof(CT) + 256 * sizeof(CT) + 16 * sizeof(int);
@@ -528,8 +983,10 @@ static cudaError_t launch_cfg(SolveArgsT<CT> a, int q, const SolveCfg& c, cudaSt
   int threads;
   size_t smem;
   if (!shape_for(a, c, &threads, &smem)) return cudaErrorInvalidValue;
-#define IE_SOLVE_CASE(NC_, SPT_) \
-  if (c.nc == NC_ && c.spt == SPT_) return launch_solve_t<CT, NC_, SPT_>(a, q, threads, smem, s);
+#define IE_SOLVE_CASE(NC_, SPT_)                                                             \
+  if (c.nc == NC_ && c.spt == SPT_)                                                          \
+    return c.pipe ? launch_pipe_t<CT, NC_, SPT_>(a, q, threads, smem, s)                     \
+                  : launch_solve_t<CT, NC_, SPT_>(a, q, threads, smem, s);
   IE_SOLVE_CASE(1, 1) IE_SOLVE_CASE(2, 1) IE_SOLVE_CASE(4, 1)
   IE_SOLVE_CASE(1, 2) IE_SOLVE_CASE(2, 2) IE_SOLVE_CASE(4, 2)
   if constexpr (sizeof(CT) == sizeof(float2)) {
@@ -590,7 +1047,7 @@ static cudaError_t launch_tuned(const SolveArgsT<CT>& a, int q, cudaStream_t s) 
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const bool fp32 = sizeof(CT) == sizeof(float2);
   const int spt0 = ((a.kv > NB ? a.kv : NB) > 576) ? 2 : 1;
-  const SolveCfg dflt{pick_nc(q, a.k, sms, fp32 ? 8 : 4), spt0, 6};
+  const SolveCfg dflt{pick_nc(q, a.k, sms, fp32 ? 8 : 4), spt0, 6, 0};
   if (!tune_enabled()) return launch_cfg(a, q, dflt, s);
   int kb = 1;
   while (kb < a.k) kb *= 2;
@@ -601,16 +1058,27 @@ static cudaError_t launch_tuned(const SolveArgsT<CT>& a, int q, cudaStream_t s) 
     std::lock_guard<std::mutex> lk(g_tune_mu);
     TuneState& T = g_tune[key];
     if (T.cand.empty()) {
-      std::vector<SolveCfg> c = {dflt, {2, 2, 3}, {4, 2, 3}, {2, 1, 3}, {1, 2, 3}, {4, 1, 3}};
+      std::vector<SolveCfg> c = {dflt, {2, 2, 3, 0}, {4, 2, 3, 0}, {2, 1, 3, 0}, {1, 2, 3, 0},
+                                 {4, 1, 3, 0}};
       if (fp32) {
-        c.push_back({8, 1, 3});
-        c.push_back({8, 2, 2});
-        c.push_back({2, 2, 2});
+        c.push_back({8, 1, 3, 0});
+        c.push_back({8, 2, 2, 0});
+        c.push_back({2, 2, 2, 0});
+      }
+      // the warp-specialised kernel
+      c.push_back({dflt.nc, spt0, 4, 1});
+      c.push_back({2, spt0, 4, 1});
+      c.push_back({4, 2, 4, 1});
+      c.push_back({2, 2, 4, 1});
+      if (fp32) {
+        c.push_back({8, spt0, 4, 1});
+        c.push_back({8, 2, 3, 1});
       }
       for (const SolveCfg& x : c) {
         if (x.spt < spt0) continue;
         bool dup = false;
-        for (const SolveCfg& y : T.cand) dup |= (y.nc == x.nc && y.spt == x.spt && y.stages == x.stages);
+        for (const SolveCfg& y : T.cand)
+          dup |= (y.nc == x.nc && y.spt == x.spt && y.stages == x.stages && y.pipe == x.pipe);
         if (!dup) T.cand.push_back(x);
       }
       T.e0.resize(T.cand.size());
@@ -640,8 +1108,8 @@ static cudaError_t launch_tuned(const SolveArgsT<CT>& a, int q, cudaStream_t s) 
           fprintf(stderr, "band solve tuner (elem %d B, kl %d, q %d, k <= %d):", key.esize, key.kl,
                   key.q, key.kb);
           for (size_t i = 0; i < T.cand.size(); ++i)
-            fprintf(stderr, " [nc %d spt %d stages %d: %.3f ms]", T.cand[i].nc, T.cand[i].spt,
-                    T.cand[i].stages, T.ms[i]);
+            fprintf(stderr, " [%s nc %d spt %d stages %d: %.3f ms]", T.cand[i].pipe ? "pipe" : "sync",
+                    T.cand[i].nc, T.cand[i].spt, T.cand[i].stages, T.ms[i]);
           fprintf(stderr, " -> %d\n", b);
         }
       } else if (T.next < (int)T.cand.size()) {
