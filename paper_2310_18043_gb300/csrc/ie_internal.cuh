@@ -127,6 +127,26 @@ cudaError_t launch_band_solve(int q, int64_t n, int kl, int64_t n_pad, const cpl
                               const cplx* Ub, const cplx* d_weights, const cplx* RHS, int64_t ldr,
                               int k, cplx* Xp, int64_t ldx, int64_t xstride, int* status,
                               cudaStream_t s);
+// Batched band solves of many problems in one launch per element type. Each add_* takes the
+// arguments of launch_band_solve / launch_band_solve32 for one problem; launch issues them.
+struct BandSolveBatch;
+BandSolveBatch* band_solve_batch_create();
+void band_solve_batch_destroy(BandSolveBatch* b);
+void band_solve_batch_clear(BandSolveBatch* b);
+int band_solve_batch_size(const BandSolveBatch* b);
+void band_solve_batch_add64(BandSolveBatch* b, int q, int64_t n, int kl, int64_t n_pad,
+                            const cplx* L64, const cplx* U64, const int* piv, const cplx* dinv,
+                            const cplx* Tb, const int* Hb, const cplx* Ub, const cplx* d_weights,
+                            const cplx* RHS, int64_t ldr, int k, cplx* Xp, int64_t ldx,
+                            int64_t xstride, int* status);
+void band_solve_batch_add32(BandSolveBatch* b, int q, int64_t n, int kl, int64_t n_pad,
+                            const float2* L32, int64_t ldl, const float2* U32, int64_t ldu,
+                            const int* piv, const float2* dinv32, const float2* T32,
+                            const int* Hb, const float2* Ui32, const cplx* d_weights,
+                            const float2* RHS, int64_t ldr, int64_t rstride, int k, float2* Y32,
+                            int64_t ldy, int64_t ystride, cplx* X, int64_t ldx, int64_t xstride,
+                            int accumulate, int* status);
+cudaError_t band_solve_batch_launch(BandSolveBatch* b, cudaStream_t s);
 // Per (pole, 8-column panel): forward 16x16 transform T with its member rows H, backward
 // inverse of the 8x8 diagonal block of U (complex128; complex64 copies when T32/Ui32 != null).
 void launch_block_transforms(int q, int64_t n, int64_t n_pad, int kl, int ldab, const cplx* AB,

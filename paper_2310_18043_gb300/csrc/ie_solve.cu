@@ -14,6 +14,7 @@
 // Factor columns (L parts forward, U parts backward, with pivots / 1/u_jj) are staged NB at a
 // time into a shared ring by cp.async.bulk (TMA bulk copies) with mbarrier completion; every
 // wait is bounded.
+#include <algorithm>
 #include <cstdio>
 #include <cstdlib>
 #include <map>
@@ -29,6 +30,26 @@ using namespace iebulk;
 namespace {
 constexpr int NB = 8;   // factor columns per staged panel = backward block
 }  // namespace
+
+// The short dense products of a panel -- H <- T H over the 16 members (forward) and
+// x_head = inv(U_block) h_head over the NB head rows (backward) -- are summed in four fixed
+// partial ranges (members 4g..4g+3, head rows 2g..2g+1), then the partials are added in a
+// fixed order. The synchronised kernel computes the four partials on four different warps
+// (one per SM sub-partition), the warp-specialised kernel on one warp; the order of every
+// floating-point operation is the same in both, so every launch shape gives identical
+// results.
+constexpr int NPART = 4;
+template <typename CT>
+__device__ __forceinline__ CT sum_parts(const CT* part, int stride, int o) {
+  CT s = part[o];
+#pragma unroll
+  for (int g = 1; g < NPART; ++g) {
+    const CT x = part[g * stride + o];
+    s.x += x.x;
+    s.y += x.y;
+  }
+  return s;
+}
 
 template <typename CT>
 struct SolveArgsT {
@@ -72,10 +93,10 @@ struct SolveArgsT {
 // (S rows further on, not yet touched by any solved column). Keeping the head out of the
 // register window makes the thread count S / SPT (a multiple of 4 warps for kl = 256 or
 // 512), so every sub-partition of the SM gets the same share of the update.
-template <typename CT, int NC, int SPT, int REGS>
-__global__ void __maxnreg__(REGS) band_solve_kernel(SolveArgsT<CT> a) {
-  const int pole = blockIdx.y;
-  const int c0 = blockIdx.x * NC;
+// One CTA's work: pole `pole`, right-hand sides grp*NC .. grp*NC+NC-1 of the solve `a`.
+template <typename CT, int NC, int SPT>
+__device__ __forceinline__ void solve_cta(const SolveArgsT<CT>& a, const int pole, const int grp) {
+  const int c0 = grp * NC;
   const int ncol = min(NC, a.k - c0);
   const int T = blockDim.x, tid = threadIdx.x;
   const int kl = a.kl, kv = a.kv, klp = a.klp, kvp = a.kvp;
@@ -98,7 +119,9 @@ __global__ void __maxnreg__(REGS) band_solve_kernel(SolveArgsT<CT> a) {
   CT* xs = hd + NB * NC;                                       // [NB][NC] solved head
   CT* hv = xs + NB * NC;                                       // [16][NC] forward set H
   CT* hv2 = hv + 16 * NC;                                      // [16][NC] T H
-  unsigned char* stage0 = (unsigned char*)(((uintptr_t)(hv2 + 16 * NC) + 127) & ~(uintptr_t)127);
+  CT* part = hv2 + 16 * NC;                                    // [NPART][16][NC] partials
+  unsigned char* stage0 =
+      (unsigned char*)(((uintptr_t)(part + NPART * 16 * NC) + 127) & ~(uintptr_t)127);
   const size_t fwd_cols_bytes = (size_t)NB * klp * sizeof(CT);
   const size_t bwd_cols_bytes = (size_t)NB * kvp * sizeof(CT);
   const size_t fwd_bytes = fwd_cols_bytes + 256 * sizeof(CT) + 16 * sizeof(int);
@@ -194,18 +217,51 @@ __global__ void __maxnreg__(REGS) band_solve_kernel(SolveArgsT<CT> a) {
         for (int c = 0; c < NC; ++c) hv[mem[u] * NC + c] = v[u][c];
     }
     __syncthreads();
-    // (B) H <- T H; the head rows' results are final: y
+    // (B) H <- T H in NPART partial sums, then their fixed-order sum; the head rows' results
+    // are final: y. FP64: the partials on consecutive warps (spread over the SM
+    // sub-partitions, whose FP64 units are the bound), one more barrier; FP32: one thread
+    // computes all partials of its output (latency, not throughput, bounds this step).
+    if constexpr (sizeof(CT) == sizeof(float2)) {
+      for (int e = tid; e < 16 * NC; e += T) {
+        const int i = e / NC, c = e - (e / NC) * NC;
+        if (Hst[i] >= 0) {
+          CT p[NPART];
+#pragma unroll
+          for (int g = 0; g < NPART; ++g) {
+            p[g] = zero;
+#pragma unroll
+            for (int m = 4 * g; m < 4 * g + 4; ++m)
+              if (Hst[m] >= 0) p[g] = cfma(Tst[i * 16 + m], hv[m * NC + c], p[g]);
+          }
+          const CT acc = sum_parts(p, 1, 0);
+          hv2[e] = acc;
+          if (i < nvalid && c < ncol) Yo[(int64_t)(c0 + c) * a.ldy + j0 + i] = acc;
+        }
+      }
+      __syncthreads();
+    } else {
+    for (int e = tid; e < NPART * 16 * NC; e += T) {
+      const int g = e / (16 * NC), o = e - g * (16 * NC);
+      const int i = o / NC, c = o - (o / NC) * NC;
+      CT acc = zero;
+      if (Hst[i] >= 0) {
+#pragma unroll
+        for (int m = 4 * g; m < 4 * g + 4; ++m)
+          if (Hst[m] >= 0) acc = cfma(Tst[i * 16 + m], hv[m * NC + c], acc);
+      }
+      part[e] = acc;
+    }
+    __syncthreads();
     for (int e = tid; e < 16 * NC; e += T) {
       const int i = e / NC, c = e - (e / NC) * NC;
       if (Hst[i] >= 0) {
-        CT acc = zero;
-        for (int m = 0; m < 16; ++m)
-          if (Hst[m] >= 0) acc = cfma(Tst[i * 16 + m], hv[m * NC + c], acc);
-        hv2[i * NC + c] = acc;
+        const CT acc = sum_parts(part, 16 * NC, e);
+        hv2[e] = acc;
         if (i < nvalid && c < ncol) Yo[(int64_t)(c0 + c) * a.ldy + j0 + i] = acc;
       }
     }
     __syncthreads();
+    }
     // (C)
 #pragma unroll
     for (int u = 0; u < SPT; ++u) {
@@ -311,14 +367,11 @@ __global__ void __maxnreg__(REGS) band_solve_kernel(SolveArgsT<CT> a) {
     const CT* Uist = (const CT*)(stage0 + (size_t)st * stage_bytes + bwd_cols_bytes);
     const int64_t j0 = a.n_pad - 1 - Bp * NB;
     // head rows j0 - t (t = 0..NB-1) = block rows NB-1-t; matrix column j0 - s2 is stage
-    // column NB-1-s2. x_head = inv(U_block) h_head, one (row, column) per thread; the head
-    // rows leave with x
-    for (int e = tid; e < NB * NC; e += T) {
+    // column NB-1-s2. x_head = inv(U_block) h_head in NPART partial sums over the head rows
+    // (FP64: one warp each for NC = 4, then a barrier; FP32: all in one thread), then their
+    // fixed-order sum; the head rows leave with x
+    auto head_out = [&](int e, CT acc) {
       const int t = e / NC, c = e - (e / NC) * NC;
-      CT acc = zero;
-#pragma unroll
-      for (int t2 = 0; t2 < NB; ++t2)
-        acc = cfma(Uist[(NB - 1 - t) * NB + (NB - 1 - t2)], hd[t2 * NC + c], acc);
       xs[t * NC + c] = acc;
       const int64_t r = j0 - t;
       if (r < n && c < ncol) {
@@ -328,6 +381,32 @@ __global__ void __maxnreg__(REGS) band_solve_kernel(SolveArgsT<CT> a) {
         if (a.mode == 1) Xo[(int64_t)(c0 + c) * a.ldx + r] = to_d(acc);
         else if (a.mode == 3) Yo[(int64_t)(c0 + c) * a.ldy + r] = acc;   // y of row r is read
       }
+    };
+    if constexpr (sizeof(CT) == sizeof(float2)) {
+      for (int e = tid; e < NB * NC; e += T) {
+        const int t = e / NC, c = e - (e / NC) * NC;
+        CT p[NPART];
+#pragma unroll
+        for (int g = 0; g < NPART; ++g) {
+          p[g] = zero;
+#pragma unroll
+          for (int t2 = 2 * g; t2 < 2 * g + 2; ++t2)
+            p[g] = cfma(Uist[(NB - 1 - t) * NB + (NB - 1 - t2)], hd[t2 * NC + c], p[g]);
+        }
+        head_out(e, sum_parts(p, 1, 0));
+      }
+    } else {
+      for (int e = tid; e < NPART * NB * NC; e += T) {
+        const int g = e / (NB * NC), o = e - g * (NB * NC);
+        const int t = o / NC, c = o - (o / NC) * NC;
+        CT acc = zero;
+#pragma unroll
+        for (int t2 = 2 * g; t2 < 2 * g + 2; ++t2)
+          acc = cfma(Uist[(NB - 1 - t) * NB + (NB - 1 - t2)], hd[t2 * NC + c], acc);
+        part[e] = acc;
+      }
+      __syncthreads();
+      for (int e = tid; e < NB * NC; e += T) head_out(e, sum_parts(part, NB * NC, e));
     }
     __syncthreads();
 #pragma unroll
@@ -368,6 +447,23 @@ __global__ void __maxnreg__(REGS) band_solve_kernel(SolveArgsT<CT> a) {
     for (int st = 0; st < a.nstage; ++st)
       for (int ph = 0; ph < 2; ++ph) mbar_wait_bounded(smem_u32(&mbar[st]), (uint32_t)ph);
   }
+}
+
+template <typename CT, int NC, int SPT, int REGS>
+__global__ void __maxnreg__(REGS) band_solve_kernel(SolveArgsT<CT> a) {
+  solve_cta<CT, NC, SPT>(a, blockIdx.y, blockIdx.x);
+}
+
+// Many independent solves (different problems: n, band, poles, block width, factors) in one
+// launch. CTA b serves solve cta[b].x, pole cta[b].y, column group cta[b].z; the block size is
+// that of the widest band, and each solve's window uses its own slot count. Every CTA's
+// arithmetic is that of band_solve_kernel for its solve.
+template <typename CT, int NC, int SPT, int REGS>
+__global__ void __maxnreg__(REGS) band_solve_batch_kernel(const SolveArgsT<CT>* items,
+                                                          const int4* cta) {
+  const int4 m = cta[blockIdx.x];
+  const SolveArgsT<CT> a = items[m.x];
+  solve_cta<CT, NC, SPT>(a, m.y, m.z);
 }
 
 // ----------------------------------------------------------------------------------------------
@@ -555,10 +651,15 @@ __global__ void __maxnreg__(REGS) band_solve_pipe_kernel(SolveArgsT<CT> a) {
       for (int e = lane; e < 16 * NC; e += 32) {
         const int i = e / NC, c = e - (e / NC) * NC;
         if (Hst[i] >= 0) {
-          CT acc = zero;
-#pragma unroll 4
-          for (int m = 0; m < 16; ++m)
-            if (Hst[m] >= 0) acc = cfma(Tst[i * 16 + m], hv[m * NC + c], acc);
+          CT p[NPART];
+#pragma unroll
+          for (int g = 0; g < NPART; ++g) {
+            p[g] = zero;
+#pragma unroll
+            for (int m = 4 * g; m < 4 * g + 4; ++m)
+              if (Hst[m] >= 0) p[g] = cfma(Tst[i * 16 + m], hv[m * NC + c], p[g]);
+          }
+          const CT acc = sum_parts(p, 1, 0);
           hv2[i * NC + c] = acc;
           if (i < nvalid && c < ncol) Yo[(int64_t)(c0 + c) * a.ldy + j0 + i] = acc;
         }
@@ -695,10 +796,15 @@ __global__ void __maxnreg__(REGS) band_solve_pipe_kernel(SolveArgsT<CT> a) {
         const int64_t j0 = a.n_pad - 1 - Bp * NB;
         for (int e = lane; e < NB * NC; e += 32) {
           const int t = e / NC, c = e - (e / NC) * NC;
-          CT acc = zero;
+          CT p[NPART];
 #pragma unroll
-          for (int t2 = 0; t2 < NB; ++t2)
-            acc = cfma(Uist[(NB - 1 - t) * NB + (NB - 1 - t2)], hd[t2 * NC + c], acc);
+          for (int g = 0; g < NPART; ++g) {
+            p[g] = zero;
+#pragma unroll
+            for (int t2 = 2 * g; t2 < 2 * g + 2; ++t2)
+              p[g] = cfma(Uist[(NB - 1 - t) * NB + (NB - 1 - t2)], hd[t2 * NC + c], p[g]);
+          }
+          const CT acc = sum_parts(p, 1, 0);
           xs[t * NC + c] = acc;
           const int64_t r = j0 - t;
           if (r < n && c < ncol) {
@@ -967,8 +1073,9 @@ static bool shape_for(SolveArgsT<CT>& a, const SolveCfg& c, int* threads, size_t
   const size_t fwdb = (size_t)NB * a.klp * sizeof(CT) + 256 * sizeof(CT) + 16 * sizeof(int);
   const size_t bwdb = (size_t)NB * a.kvp * sizeof(CT) + 64 * sizeof(CT);
   const size_t stage_bytes = ((fwdb > bwdb ? fwdb : bwdb) + 127) & ~(size_t)127;
-  // mbarriers, then hd and xs [NB][NC], hv and hv2 [16][NC], alignment slack
-  const size_t fixed = 128 + (size_t)(2 * NB + 32) * c.nc * sizeof(CT) + 256;
+  // mbarriers, then hd and xs [NB][NC], hv and hv2 [16][NC], partials [NPART][16][NC],
+  // alignment slack
+  const size_t fixed = 128 + (size_t)(2 * NB + 32 + NPART * 16) * c.nc * sizeof(CT) + 256;
   const size_t budget = 200 * 1024;
   if (fixed + 2 * stage_bytes > budget) return false;
   int nstage = (int)((budget - fixed) / stage_bytes);
@@ -1176,4 +1283,166 @@ cudaError_t launch_band_solve32(int q, int64_t n, int kl, int64_t n_pad, const f
   a.X = X; a.ldx = ldx; a.xstride = xstride;
   a.status = status;
   return launch_tuned(a, q, s);
+}
+
+// ----------------------------------------------------------------------------------------------
+// Batched band solves: the solves of many problems in one launch per element type
+// (band_solve_batch_kernel). Each added solve is described exactly as launch_band_solve /
+// launch_band_solve32 would launch it; the launch uses one shape for all of them (NC = 4 right-
+// hand sides per CTA, the block size of the widest band) and gives each solve the staged panels
+// that fit the common shared-memory size. CTAs are ordered by decreasing work so the longest
+// solves start first.
+struct BandSolveBatch {
+  std::vector<SolveArgsT<cplx>> a64;
+  std::vector<int> q64;
+  std::vector<SolveArgsT<float2>> a32;
+  std::vector<int> q32;
+  void* d_items = nullptr;
+  size_t items_cap = 0;
+  int4* d_cta = nullptr;
+  size_t cta_cap = 0;
+  std::vector<int4> cta;
+};
+
+BandSolveBatch* band_solve_batch_create() { return new BandSolveBatch(); }
+void band_solve_batch_destroy(BandSolveBatch* b) {
+  if (!b) return;
+  cudaFree(b->d_items);
+  cudaFree(b->d_cta);
+  delete b;
+}
+void band_solve_batch_clear(BandSolveBatch* b) {
+  b->a64.clear();
+  b->q64.clear();
+  b->a32.clear();
+  b->q32.clear();
+}
+int band_solve_batch_size(const BandSolveBatch* b) { return (int)(b->a64.size() + b->a32.size()); }
+
+void band_solve_batch_add64(BandSolveBatch* b, int q, int64_t n, int kl, int64_t n_pad,
+                            const cplx* L64, const cplx* U64, const int* piv, const cplx* dinv,
+                            const cplx* Tb, const int* Hb, const cplx* Ub, const cplx* d_weights,
+                            const cplx* RHS, int64_t ldr, int k, cplx* Xp, int64_t ldx,
+                            int64_t xstride, int* status) {
+  if (k <= 0) return;
+  SolveArgsT<cplx> a{};
+  a.n = n; a.n_pad = n_pad; a.kl = kl; a.kv = 2 * kl; a.klp = kl; a.kvp = 2 * kl; a.k = k;
+  a.mode = 0;
+  a.L = L64; a.U = U64; a.ldl = kl; a.ldu = 2 * kl;
+  a.lstride = n_pad * kl; a.ustride = n_pad * 2 * kl;
+  a.piv = piv; a.dinv = dinv; a.weights = d_weights;
+  a.Tb = Tb; a.Hb = Hb; a.Ub = Ub;
+  a.RHS = RHS; a.ldr = ldr; a.rstride = 0;
+  a.Y = Xp; a.ldy = ldx; a.ystride = xstride;
+  a.X = Xp; a.ldx = ldx; a.xstride = xstride;
+  a.status = status;
+  b->a64.push_back(a);
+  b->q64.push_back(q);
+}
+
+void band_solve_batch_add32(BandSolveBatch* b, int q, int64_t n, int kl, int64_t n_pad,
+                            const float2* L32, int64_t ldl, const float2* U32, int64_t ldu,
+                            const int* piv, const float2* dinv32, const float2* T32,
+                            const int* Hb, const float2* Ui32, const cplx* d_weights,
+                            const float2* RHS, int64_t ldr, int64_t rstride, int k, float2* Y32,
+                            int64_t ldy, int64_t ystride, cplx* X, int64_t ldx, int64_t xstride,
+                            int accumulate, int* status) {
+  if (k <= 0) return;
+  SolveArgsT<float2> a{};
+  a.n = n; a.n_pad = n_pad; a.kl = kl; a.kv = 2 * kl;
+  a.klp = (int)ldl; a.kvp = (int)ldu;
+  a.k = k; a.mode = accumulate ? 3 : 1;
+  a.L = L32; a.U = U32; a.ldl = ldl; a.ldu = ldu;
+  a.lstride = n_pad * ldl; a.ustride = n_pad * ldu;
+  a.piv = piv; a.dinv = dinv32; a.weights = d_weights;
+  a.Tb = T32; a.Hb = Hb; a.Ub = Ui32;
+  a.RHS = RHS; a.ldr = ldr; a.rstride = rstride;
+  a.Y = Y32; a.ldy = ldy; a.ystride = ystride;
+  a.X = X; a.ldx = ldx; a.xstride = xstride;
+  a.status = status;
+  b->a32.push_back(a);
+  b->q32.push_back(q);
+}
+
+template <typename CT, int SPT, int REGS>
+static cudaError_t batch_launch_r(BandSolveBatch* b, std::vector<SolveArgsT<CT>>& items,
+                                  int threads, size_t smem, cudaStream_t s) {
+  auto kfn = band_solve_batch_kernel<CT, 4, SPT, REGS>;
+  cudaError_t e = ie_smem_optin((const void*)kfn);
+  if (e != cudaSuccess) return e;
+  int blocks = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, kfn, threads, smem);
+  if (e != cudaSuccess) return e;
+  if (blocks < 1) return cudaErrorLaunchOutOfResources;
+  const size_t ib = items.size() * sizeof(SolveArgsT<CT>);
+  if (ib > b->items_cap) {
+    cudaFree(b->d_items);
+    b->d_items = nullptr;
+    e = cudaMalloc(&b->d_items, ib);
+    if (e != cudaSuccess) { b->items_cap = 0; return e; }
+    b->items_cap = ib;
+  }
+  if (b->cta.size() > b->cta_cap) {
+    cudaFree(b->d_cta);
+    b->d_cta = nullptr;
+    e = cudaMalloc(&b->d_cta, b->cta.size() * sizeof(int4));
+    if (e != cudaSuccess) { b->cta_cap = 0; return e; }
+    b->cta_cap = b->cta.size();
+  }
+  // pageable sources: the copies complete before cudaMemcpyAsync returns to the host
+  e = cudaMemcpyAsync(b->d_items, items.data(), ib, cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) return e;
+  e = cudaMemcpyAsync(b->d_cta, b->cta.data(), b->cta.size() * sizeof(int4),
+                      cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) return e;
+  kfn<<<(unsigned)b->cta.size(), threads, smem, s>>>((const SolveArgsT<CT>*)b->d_items, b->d_cta);
+  ie_count_launch();
+  return cudaGetLastError();
+}
+
+template <typename CT>
+static cudaError_t batch_launch_t(BandSolveBatch* b, std::vector<SolveArgsT<CT>>& items,
+                                  const std::vector<int>& qs, cudaStream_t s) {
+  if (items.empty()) return cudaSuccess;
+  constexpr int NCB = 4;
+  int slots = NB;
+  for (auto& a : items) slots = std::max(slots, a.kv);
+  const int spt = slots > 576 ? 2 : 1;
+  if ((slots + spt - 1) / spt > 576) return cudaErrorInvalidValue;
+  const int threads = ((slots + spt - 1) / spt + 31) / 32 * 32;
+  const size_t fixed = 128 + (size_t)(2 * NB + 32 + NPART * 16) * NCB * sizeof(CT) + 256;
+  const size_t budget = 200 * 1024;
+  size_t smem = 0;
+  for (auto& a : items) {
+    const size_t fwdb = (size_t)NB * a.klp * sizeof(CT) + 256 * sizeof(CT) + 16 * sizeof(int);
+    const size_t bwdb = (size_t)NB * a.kvp * sizeof(CT) + 64 * sizeof(CT);
+    const size_t st = ((fwdb > bwdb ? fwdb : bwdb) + 127) & ~(size_t)127;
+    if (fixed + 2 * st > budget) return cudaErrorInvalidValue;
+    int ns = (int)((budget - fixed) / st);
+    if (ns > 6) ns = 6;
+    a.nstage = ns;
+    smem = std::max(smem, fixed + (size_t)ns * st);
+  }
+  // CTAs, longest solves first (work ~ n * (kl + kv) per CTA)
+  std::vector<int> ord(items.size());
+  for (size_t i = 0; i < ord.size(); ++i) ord[i] = (int)i;
+  std::stable_sort(ord.begin(), ord.end(), [&](int x, int y) {
+    return items[x].n * (items[x].kl + items[x].kv) > items[y].n * (items[y].kl + items[y].kv);
+  });
+  b->cta.clear();
+  for (int i : ord)
+    for (int p = 0; p < qs[i]; ++p)
+      for (int g = 0; g * NCB < items[i].k; ++g) b->cta.push_back(make_int4(i, p, g, 0));
+  if (spt == 1) {
+    if (threads <= 16 * 32) return batch_launch_r<CT, 1, 112>(b, items, threads, smem, s);
+    return batch_launch_r<CT, 1, 96>(b, items, threads, smem, s);
+  }
+  if (threads <= 16 * 32) return batch_launch_r<CT, 2, 112>(b, items, threads, smem, s);
+  return batch_launch_r<CT, 2, 96>(b, items, threads, smem, s);
+}
+
+cudaError_t band_solve_batch_launch(BandSolveBatch* b, cudaStream_t s) {
+  cudaError_t e = batch_launch_t(b, b->a64, b->q64, s);
+  if (e != cudaSuccess) return e;
+  return batch_launch_t(b, b->a32, b->q32, s);
 }
