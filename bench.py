@@ -482,9 +482,11 @@ def compact_results(solves, mixed, c4, batch, simple, sens, roofline, cpu):
         out["simple_rule_tta_s"] = r3(simple["seconds"])
     if batch and "speedup" in batch:
         out["batch_speedup_c128"] = r3(batch["speedup"])
+        out["batch_fused_speedup_c128"] = r3(batch.get("speedup_fused"))
         bm = batch.get("mixed_precision") or {}
         if "speedup" in bm:
             out["batch_speedup_mixed"] = r3(bm["speedup"])
+            out["batch_fused_speedup_mixed"] = r3(bm.get("speedup_fused"))
     if sens and (sens.get("band_solve_adj_c128") or {}).get("frac"):
         out["adj_solve_frac_fp64"] = r3(sens["band_solve_adj_c128"]["frac"])
     out["solve_frac_fp64"] = r3(roofline.get("frac"))
@@ -627,6 +629,13 @@ def time_batch(ie, device, stream, workers=12, precision=0):
     stb, res = ie.ie_solve_batch(probs, max_workers=workers)
     torch.cuda.synchronize()
     t_bat = time.perf_counter() - t0
+    # all problems in lockstep: one batched band-solve launch per Arnoldi step
+    t0 = time.perf_counter()
+    stf, resf = ie.ie_solve_batch_fused(probs, stream)
+    torch.cuda.synchronize()
+    t_fused = time.perf_counter() - t0
+    same_fused = all(r["n_found"] == s_[2] and np.allclose(r["lam"][:s_[2]], s_[1], rtol=1e-10, atol=0)
+                     for r, s_ in zip(resf, seq))
     same = all(r["n_found"] == s_[2] and np.allclose(r["lam"][:s_[2]], s_[1], rtol=1e-12, atol=0)
                for r, s_ in zip(res, seq))
     errs = []
@@ -640,9 +649,12 @@ def time_batch(ie, device, stream, workers=12, precision=0):
             "max_rho": max((float(np.max(r["rho"][: r["n_found"]])) for r in res if r["n_found"]),
                            default=None),
             "create_s_total": t_create,
-            "sequential_s": t_seq, "batched_s": t_bat,
+            "sequential_s": t_seq, "batched_s": t_bat, "fused_s": t_fused,
             "problems_per_s_sequential": len(names) / t_seq,
-            "problems_per_s_batched": len(names) / t_bat, "speedup": t_seq / t_bat,
+            "problems_per_s_batched": len(names) / t_bat,
+            "problems_per_s_fused": len(names) / t_fused, "speedup": t_seq / t_bat,
+            "speedup_fused": t_seq / t_fused, "status_fused": ie.ie_status_str(stf),
+            "fused_same_as_sequential": bool(same_fused),
             "status": ie.ie_status_str(stb), "same_as_sequential": bool(same),
             "n_found": [r["n_found"] for r in res],
             "n_in_disk_reference": [len(x) for x in refs],

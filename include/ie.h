@@ -305,6 +305,21 @@ typedef struct {
  * Not in the paper. */
 ie_status ie_solve_batch(ie_batch_item* items, int32_t nb, int32_t max_workers);
 
+/* ie_solve_batch_fused: the same results as ie_solve_batch, with every item's driver advancing
+ * in lockstep on one stream. Each Arnoldi step applies G (Eq. linearsolve2) to the active
+ * columns of every item with one band-solve launch per factor precision for all items
+ * together (a problem table on the device: each CTA serves one (item, pole, column group)),
+ * then each item's Krylov kernels run, and one stream synchronisation serves every item's
+ * convergence test. Mixed-precision items refine in lockstep, each to its own accuracy. An
+ * item whose filter is complete runs its HSRR and stop test (Sec. 3.2) and either finishes or
+ * starts its next outer iteration (Alg. 1 or Alg. 2, opts.driver of its handle) while the
+ * others keep stepping. Every handle must be on the current device; items[i].stream is
+ * ignored (stream is used for all). Returns IE_ERR_ARG for nb < 1, a NULL item field that
+ * ie_solve requires, two items sharing a handle or a handle on another device (nothing runs);
+ * otherwise IE_OK if every item returned IE_OK, else the first non-OK item status in item
+ * order. Not in the paper (the paper notes disks are independent problems, Sec. 1). */
+ie_status ie_solve_batch_fused(ie_batch_item* items, int32_t nb, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -1195,6 +1195,431 @@ extern "C" ie_status ie_solve_batch(ie_batch_item* items, int32_t nb, int32_t ma
   return IE_OK;
 }
 
+// ------------------------------ fused batch ----------------------------------------------------
+// All problems of a batch advance together: every Arnoldi step applies G to the active columns
+// of every problem with ONE band-solve launch per element type (band_solve_batch_kernel), the
+// per-problem Krylov kernels follow on the same stream, and one synchronisation serves all
+// problems' convergence tests. A problem whose filter is complete runs its HSRR and stop test,
+// then either finishes or starts its next outer iteration while the others keep stepping.
+namespace {
+struct GReq {
+  ie_handle h;
+  const cplx* V;
+  int64_t ldv;
+  const int64_t* d_off;
+  int k;
+  cplx* GV;
+  int64_t ldg;
+};
+
+// pinned host scratch, reused across calls of one fused solve
+struct Pinned {
+  void* p = nullptr;
+  size_t cap = 0;
+  ~Pinned() { if (p) cudaFreeHost(p); }
+  void* get(size_t bytes) {
+    if (bytes > cap) {
+      if (p) cudaFreeHost(p);
+      p = nullptr;
+      cap = 0;
+      if (cudaMallocHost(&p, bytes) != cudaSuccess) return nullptr;
+      cap = bytes;
+    }
+    return p;
+  }
+};
+}  // namespace
+
+// G applied to every request (Eq. linearsolve2), one batched band-solve launch per element type
+// (complex128, complex64); mixed-precision requests refine in lockstep, each until its own
+// target (as apply_G_mixed), with one synchronisation per refinement step for all of them.
+static ie_status apply_G_batch(std::vector<GReq>& reqs, BandSolveBatch* bb, Pinned& pin,
+                               cudaStream_t s) {
+  if (reqs.empty()) return IE_OK;
+  band_solve_batch_clear(bb);
+  std::vector<size_t> mixed;
+  for (size_t r = 0; r < reqs.size(); ++r) {
+    GReq& g = reqs[r];
+    ie_handle h = g.h;
+    launch_spmv(h->pen(), make_double2(0, 0), make_double2(1, 0), g.V, g.ldv, g.d_off, g.k,
+                h->BVw, h->n, s);
+    const int64_t ps = h->n * (int64_t)h->kmax;
+    if (h->precision == 0) {
+      band_solve_batch_add64(bb, h->q, h->n, h->kl, h->n_pad, h->L64, h->U64, h->piv, h->dinv,
+                             h->Tb, h->Hb, h->Uinvb, h->d_weights, h->BVw, h->n, g.k, h->Xp,
+                             h->n, ps, h->status);
+    } else {
+      launch_to_c64(h->n, g.k, h->BVw, h->n, h->BV32, h->n, s);
+      band_solve_batch_add32(bb, h->q, h->n, h->kl, h->n_pad, h->L32, h->klp, h->U32, h->kv,
+                             h->piv, h->dinv32, h->T32, h->Hb, h->Ub32, h->d_weights, h->BV32,
+                             h->n, 0, g.k, h->Y32, h->n, ps, h->Xp, h->n, ps, 0, h->status);
+      mixed.push_back(r);
+    }
+  }
+  CK(band_solve_batch_launch(bb, s));
+  // lockstep FP64 refinement of the mixed-precision requests (see apply_G_mixed)
+  struct Ref { size_t r; double prev, last; bool on; };
+  std::vector<Ref> ref;
+  for (size_t r : mixed) {
+    ie_handle h = reqs[r].h;
+    const bool skip = h->ref_eps0 > 0.0 && 10.0 * h->ref_eps0 <= h->refine_target;
+    ref.push_back({r, -1.0, 0.0, !skip && h->refine > 0});
+  }
+  for (int it = 1;; ++it) {
+    bool any = false;
+    band_solve_batch_clear(bb);
+    size_t off = 0;
+    std::vector<size_t> offs(ref.size(), 0);
+    for (size_t i = 0; i < ref.size(); ++i) {
+      Ref& f = ref[i];
+      ie_handle h = reqs[f.r].h;
+      if (!f.on || it > h->refine) { f.on = false; continue; }
+      any = true;
+      const int k = reqs[f.r].k;
+      const int64_t n = h->n, ps = n * (int64_t)h->kmax;
+      launch_pole_residual(h->pen(), h->d_poles, h->q, k, h->BVw, n, h->Xp, n, ps, h->R32, n,
+                           ps, s);
+      band_solve_batch_add32(bb, h->q, n, h->kl, h->n_pad, h->L32, h->klp, h->U32, h->kv, h->piv,
+                             h->dinv32, h->T32, h->Hb, h->Ub32, h->d_weights, h->R32, n, ps, k,
+                             h->Y32, n, ps, h->Xp, n, ps, 1, h->status);
+      offs[i] = off;
+      off += (size_t)h->q * k * 2;
+    }
+    if (!any) break;
+    CK(band_solve_batch_launch(bb, s));
+    unsigned* hn = (unsigned*)pin.get(off * sizeof(unsigned));
+    if (!hn) return IE_ERR_OOM;
+    for (size_t i = 0; i < ref.size(); ++i) {
+      Ref& f = ref[i];
+      if (!f.on) continue;
+      ie_handle h = reqs[f.r].h;
+      const int k = reqs[f.r].k;
+      const int64_t n = h->n, ps = n * (int64_t)h->kmax;
+      const size_t nn2 = (size_t)h->q * k * 2;
+      CK(cudaMemsetAsync(h->d_rnrm, 0, sizeof(unsigned) * nn2, s));
+      launch_refine_add(h->q, n, k, h->Y32, n, ps, h->Xp, n, ps, h->d_rnrm, s);
+      CK(cudaMemcpyAsync(hn + offs[i], h->d_rnrm, sizeof(unsigned) * nn2, cudaMemcpyDeviceToHost, s));
+    }
+    CK(cudaStreamSynchronize(s));
+    for (size_t i = 0; i < ref.size(); ++i) {
+      Ref& f = ref[i];
+      if (!f.on) continue;
+      ie_handle h = reqs[f.r].h;
+      const size_t nn2 = (size_t)h->q * reqs[f.r].k * 2;
+      h->refine_solves += 1;
+      double d = 0.0;
+      for (size_t e = 0; e < nn2; e += 2) {
+        float dm, xm;
+        std::memcpy(&dm, &hn[offs[i] + e], sizeof(float));
+        std::memcpy(&xm, &hn[offs[i] + e + 1], sizeof(float));
+        if (xm > 0.0f) d = std::max(d, (double)dm / (double)xm);
+      }
+      f.last = d;
+      if (it == 1) h->ref_eps0 = d;
+      if (f.prev > 0.0) {
+        if (d > 0.5 * f.prev) { f.on = false; continue; }
+        h->ref_c = std::min(1.0, d / f.prev);
+      }
+      const double c = f.prev > 0.0 ? d / f.prev : (h->ref_c > 0.0 ? 10.0 * h->ref_c : 1.0);
+      if (d * std::min(1.0, c) <= h->refine_target) f.on = false;
+      f.prev = d;
+    }
+  }
+  for (auto& f : ref) reqs[f.r].h->refine_last_corr = f.last;
+  for (GReq& g : reqs) {
+    ie_handle h = g.h;
+    const int64_t ps = h->n * (int64_t)h->kmax;
+    if (h->precision == 0)
+      launch_pole_sum(h->q, h->n, g.k, h->Xp, h->n, ps, g.GV, g.ldg, s);
+    else
+      launch_pole_wsum(h->q, h->n, g.k, h->Xp, h->n, ps, h->d_weights, g.GV, g.ldg, s);
+    h->g_columns += g.k;
+  }
+  return IE_OK;
+}
+
+extern "C" ie_status ie_solve_batch_fused(ie_batch_item* items, int32_t nb, void* stream) {
+  if (!items || nb < 1) return IE_ERR_ARG;
+  std::set<ie_handle> seen;
+  int dev = -1;
+  cudaGetDevice(&dev);
+  for (int i = 0; i < nb; ++i) {
+    const ie_batch_item& it = items[i];
+    if (!it.h || !it.h_lambda || !it.X_any || it.ldx < it.h->n) return IE_ERR_ARG;
+    if (it.Y0_any && it.ldy0 < it.h->n) return IE_ERR_ARG;
+    if (!seen.insert(it.h).second || it.h->dev != dev) return IE_ERR_ARG;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  BandSolveBatch* bb = band_solve_batch_create();
+  Pinned pin, pin2;
+  struct FItem {
+    ie_batch_item* it;
+    ie_handle h;
+    int phase = 0;   // 0: start a filter, 1: Arnoldi steps, 2: filter done, 3: finished
+    int t = 1, pc = 0, prev = -1, nf = 0, nshift = 0;
+    bool converged = false, reuse = false, noconv = false;
+    double rmax = 1.0, odd = 0.0;
+    std::vector<int> act;
+    std::vector<zc> lam;
+    std::vector<double> e, rho;
+    std::vector<char> filt;
+  };
+  std::vector<FItem> F(nb);
+  ie_status first_bad = IE_OK;
+  auto fail = [&](FItem& f, ie_status st) {
+    f.it->status = st;
+    f.phase = 3;
+    if (first_bad == IE_OK) first_bad = st;
+  };
+  for (int i = 0; i < nb; ++i) {
+    FItem& f = F[i];
+    f.it = &items[i];
+    f.h = items[i].h;
+    ie_handle h = f.h;
+    h->side = 0;
+    f.pc = h->p;
+    f.it->status = IE_OK;
+    f.it->n_found = 0;
+    const int k = h->kmax;
+    const int64_t n = h->n;
+    if (f.it->Y0_any) {
+      if (is_device_ptr(f.it->Y0_any))
+        launch_copy_cols(n, k, (const cplx*)f.it->Y0_any, f.it->ldy0, h->Yb, n, s);
+      else if (cudaMemcpy2DAsync(h->Yb, sizeof(cplx) * n, f.it->Y0_any, sizeof(cplx) * f.it->ldy0,
+                                 sizeof(cplx) * n, k, cudaMemcpyHostToDevice, s) != cudaSuccess) {
+        fail(f, IE_ERR_CUDA);
+        continue;
+      }
+    } else {
+      launch_random_block(n, k, h->Yb, n, h->opts.seed, 0xA5A5u, s);
+      launch_orth_cgs2(n, k, h->Yb, n, h->opts.seed, 0x5A5Au, h->hbuf, h->scratch, h->d_flags, s);
+    }
+    h->salt = 1;
+    const double t_factor = h->stats.t_factor_ms;
+    h->stats = ie_stats{};
+    h->stats.t_factor_ms = t_factor;
+  }
+  while (true) {
+    // ---- requests of this step
+    std::vector<GReq> reqs;
+    std::vector<int> starting, stepping;
+    size_t nres = 0;
+    for (int i = 0; i < nb; ++i) {
+      FItem& f = F[i];
+      ie_handle h = f.h;
+      if (f.phase == 0) {
+        const int k = h->kmax;
+        f.reuse = h->opts.driver == 2 && f.t > 1;
+        std::vector<zc> sh, cw;
+        outer_coeffs(f.pc, sh, cw, f.odd);
+        f.nshift = (int)sh.size();
+        if (ensure_shift_capacity(h, std::max(f.nshift, 1)) != IE_OK) { fail(f, IE_ERR_OOM); continue; }
+        std::vector<cplx> a(f.nshift), b(f.nshift);
+        for (int j = 0; j < f.nshift; ++j) { a[j] = to_c(sh[j]); b[j] = to_c(cw[j]); }
+        if (f.nshift) {
+          cudaMemcpyAsync(h->d_shifts, a.data(), sizeof(cplx) * f.nshift, cudaMemcpyHostToDevice, s);
+          cudaMemcpyAsync(h->d_cw, b.data(), sizeof(cplx) * f.nshift, cudaMemcpyHostToDevice, s);
+        }
+        f.noconv = false;
+        f.rmax = 1.0;
+        if (!f.reuse) {
+          h->refine_target = kRefineFull;
+          reqs.push_back({h, h->Yb, h->n, nullptr, k, h->Wb, h->n});   // Ytilde = G(Y)
+          starting.push_back(i);
+        } else {
+          // Alg. 2: the kept Krylov spaces, every shift of the doubled set re-solved
+          f.act.clear();
+          for (int c = 0; c < k; ++c) {
+            h->conv_h[c] = (h->beta_h[c] > 0.0 && f.nshift > 0) ? 0 : 1;
+            if (!h->conv_h[c] && h->jc_h[c] > 0) f.act.push_back(c);
+          }
+          if (!f.act.empty()) {
+            cudaMemcpyAsync(h->d_act, f.act.data(), sizeof(int) * f.act.size(),
+                            cudaMemcpyHostToDevice, s);
+            launch_givens(h->K, h->d_act, (int)f.act.size(), h->d_shifts, f.nshift, h->rot_c,
+                          h->rot_s, h->gvec, 1, h->d_res, s);
+            stepping.push_back(i);
+            nres += f.act.size();
+          }
+          f.phase = 1;
+        }
+      } else if (f.phase == 1) {
+        f.act.clear();
+        for (int c = 0; c < h->kmax; ++c)
+          if (!h->conv_h[c]) {
+            if (h->jc_h[c] >= h->m_max) { f.noconv = true; continue; }
+            f.act.push_back(c);
+          }
+        if (f.act.empty()) { f.phase = 2; continue; }
+        const int kact = (int)f.act.size();
+        cudaMemcpyAsync(h->d_act, f.act.data(), sizeof(int) * kact, cudaMemcpyHostToDevice, s);
+        launch_active_offsets(h->K, h->d_act, kact, h->d_off, s);
+        if (h->precision == 1) h->refine_target = std::min(1e-2, h->opts.gmres_tol / (50.0 * f.rmax));
+        reqs.push_back({h, h->K.V, h->n, h->d_off, kact, h->Wb, h->n});
+        stepping.push_back(-1 - i);   // marks an Arnoldi step (decoded below)
+        nres += kact;
+      }
+    }
+    if (!reqs.empty()) {
+      const ie_status gs = apply_G_batch(reqs, bb, pin2, s);
+      if (gs != IE_OK) {
+        for (auto& f : F) if (f.phase < 3) fail(f, gs);
+        break;
+      }
+    }
+    for (GReq& g : reqs) g.h->refine_target = kRefineFull;
+    // ---- Krylov work of this step and one read-back for all problems
+    size_t nbeta = 0;
+    for (int i : starting) nbeta += F[i].h->kmax;
+    double* hb = (double*)pin.get(sizeof(double) * (nres + nbeta + 1));
+    if (!hb) { for (auto& f : F) if (f.phase < 3) fail(f, IE_ERR_OOM); break; }
+    size_t off = 0;
+    std::vector<size_t> boff(nb, 0), roff(nb, 0);
+    for (int i : starting) {
+      ie_handle h = F[i].h;
+      launch_krylov_start(h->K, h->kmax, h->Wb, h->n, h->scratch, s);
+      boff[i] = off;
+      cudaMemcpyAsync(hb + off, h->K.beta, sizeof(double) * h->kmax, cudaMemcpyDeviceToHost, s);
+      off += h->kmax;
+    }
+    for (int code : stepping) {
+      const bool arnoldi = code < 0;
+      const int i = arnoldi ? -1 - code : code;
+      FItem& f = F[i];
+      ie_handle h = f.h;
+      const int kact = (int)f.act.size();
+      if (arnoldi) {
+        launch_arnoldi_cgs2(h->K, h->d_act, kact, h->Wb, h->n, h->hbuf, h->scratch, s);
+        launch_givens(h->K, h->d_act, kact, h->d_shifts, f.nshift, h->rot_c, h->rot_s, h->gvec, 0,
+                      h->d_res, s);
+      }
+      roff[i] = off;
+      cudaMemcpyAsync(hb + off, h->d_res, sizeof(double) * kact, cudaMemcpyDeviceToHost, s);
+      off += kact;
+    }
+    if (cudaStreamSynchronize(s) != cudaSuccess) {
+      for (auto& f : F) if (f.phase < 3) fail(f, IE_ERR_CUDA);
+      break;
+    }
+    for (int i = 0; i < nb; ++i) flush_solve_timing(F[i].h);
+    for (int i : starting) {
+      FItem& f = F[i];
+      ie_handle h = f.h;
+      const int k = h->kmax;
+      for (int c = 0; c < k; ++c) {
+        h->beta_h[c] = hb[boff[i] + c];
+        h->jc_h[c] = 0;
+        h->conv_h[c] = (h->beta_h[c] > 0.0 && f.nshift > 0) ? 0 : 1;
+      }
+      f.phase = 1;
+    }
+    for (int code : stepping) {
+      const bool arnoldi = code < 0;
+      const int i = arnoldi ? -1 - code : code;
+      FItem& f = F[i];
+      ie_handle h = f.h;
+      double rm = 0.0;
+      for (size_t a = 0; a < f.act.size(); ++a) {
+        const int c = f.act[a];
+        const double r = hb[roff[i] + a];
+        if (arnoldi) h->jc_h[c] += 1;
+        if (r <= h->opts.gmres_tol) h->conv_h[c] = 1;
+        else rm = std::max(rm, r);
+      }
+      f.rmax = rm > 0.0 ? rm : 1.0;
+    }
+    // ---- problems whose filter is complete: combine, HSRR, stop test (Sec. 3.2)
+    for (int i = 0; i < nb; ++i) {
+      FItem& f = F[i];
+      if (f.phase != 2) continue;
+      ie_handle h = f.h;
+      const int k = h->kmax;
+      const int64_t n = h->n;
+      launch_krylov_combine(h->K, k, h->d_shifts, h->d_cw, f.nshift, f.odd, h->Rscr, h->zbuf, h->Ub,
+                            n, s);
+      int mx = 0, mn = 1 << 30;
+      for (int c = 0; c < k; ++c) { mx = std::max(mx, h->jc_h[c]); mn = std::min(mn, h->jc_h[c]); }
+      h->stats.gmres_iters_max = mx;
+      h->stats.gmres_iters_min = mn;
+      h->stats.p_final = f.pc;
+      const ie_status hs = hsrr_dev(h, h->Ub, n, k, s, f.lam, f.e, f.rho);
+      if (hs != IE_OK) { fail(f, hs); continue; }
+      f.filt.assign(k, 0);
+      int nf = 0;
+      bool all_conv = true;
+      double mr = 0.0;
+      for (int j = 0; j < k; ++j) {
+        f.filt[j] = in_disk(h, f.lam[j]) && f.e[j] < h->opts.tau_g;
+        if (f.filt[j]) {
+          ++nf;
+          mr = std::max(mr, f.rho[j]);
+          if (!(f.rho[j] < h->opts.tau)) all_conv = false;
+        }
+      }
+      f.nf = nf;
+      h->stats.outer_iters = f.t;
+      h->stats.n_found = nf;
+      h->stats.max_rho_found = mr;
+      if ((f.t == 1 && nf >= 1 && all_conv) || (f.t >= 2 && nf == f.prev && all_conv)) {
+        f.converged = true;
+      } else if (f.t >= h->opts.max_outer) {
+        f.converged = false;
+      } else {
+        f.prev = nf;
+        if (h->opts.driver == 1) launch_copy_cols(n, k, h->Xh, n, h->Yb, n, s);   // Y <- Ritz vectors
+        else f.pc *= 2;                                                             // doubling step
+        f.t += 1;
+        f.phase = 0;
+        continue;
+      }
+      // outputs: filtered pairs first, each group by |lambda - c| (as ie_solve)
+      std::vector<int> ord(k);
+      std::iota(ord.begin(), ord.end(), 0);
+      auto dist = [&](int j) {
+        return (std::isfinite(f.lam[j].real()) && std::isfinite(f.lam[j].imag()))
+                   ? std::abs(f.lam[j] - h->ctr())
+                   : std::numeric_limits<double>::infinity();
+      };
+      std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) {
+        if (f.filt[a] != f.filt[b]) return f.filt[a] > f.filt[b];
+        return dist(a) < dist(b);
+      });
+      cudaMemcpyAsync(h->d_perm, ord.data(), sizeof(int) * k, cudaMemcpyHostToDevice, s);
+      const bool xdev = is_device_ptr(f.it->X_any);
+      cplx* Xo = xdev ? (cplx*)f.it->X_any : h->Ub;
+      const int64_t ldXo = xdev ? f.it->ldx : n;
+      launch_permute_cols(n, k, h->Xh, n, h->d_perm, Xo, ldXo, s);
+      if (!xdev && stage_out(h, Xo, ldXo, k, f.it->X_any, f.it->ldx, s) != IE_OK) {
+        fail(f, IE_ERR_CUDA);
+        continue;
+      }
+      const ie_status cs = check_status(h, s);
+      if (cs != IE_OK) { fail(f, cs); continue; }
+      for (int j = 0; j < k; ++j) {
+        const zc l = f.lam[ord[j]];
+        f.it->h_lambda[j].re = l.real();
+        f.it->h_lambda[j].im = l.imag();
+        if (f.it->h_rho) f.it->h_rho[j] = f.rho[ord[j]];
+        if (f.it->h_e) f.it->h_e[j] = f.e[ord[j]];
+      }
+      f.it->n_found = nf;
+      h->stats.converged = f.converged ? 1 : 0;
+      fill_solve_stats(h, &h->stats);
+      f.it->stats = h->stats;
+      f.it->status = f.converged ? IE_OK : IE_ERR_NOCONV;
+      if (!f.converged && first_bad == IE_OK) first_bad = IE_ERR_NOCONV;
+      f.phase = 3;
+    }
+    bool all_done = true;
+    for (auto& f : F) all_done &= f.phase == 3;
+    if (all_done) break;
+  }
+  band_solve_batch_destroy(bb);
+  for (int i = 0; i < nb; ++i)
+    if (items[i].status != IE_OK) return (ie_status)items[i].status;
+  return first_bad;
+}
+
 // ------------------------------ adjoint pencil --------------------------------------------------
 namespace {
 struct SideGuard {   // the adjoint side for the guard's lifetime

@@ -68,7 +68,7 @@ class ie_batch_item(C.Structure):
 EXPORTS = ["ie_opts_default", "ie_create", "ie_destroy", "ie_status_str", "ie_filter_apply",
            "ie_apply_G", "ie_hsrr", "ie_solve", "ie_spmv", "ie_get_coeffs", "ie_get_factor",
            "ie_get_stats", "ie_apply_G_static", "ie_apply_GH", "ie_solve_left",
-           "ie_eig_sensitivity", "ie_solve_batch"]
+           "ie_eig_sensitivity", "ie_solve_batch", "ie_solve_batch_fused"]
 
 _lib = None
 _vp, _i32, _i64, _dp = C.c_void_p, C.c_int32, C.c_int64, C.POINTER(C.c_double)
@@ -103,6 +103,7 @@ def load():
     L.ie_solve_left.argtypes = [_vp, _vp, _i32, _vp, _i64, _vp, _i64, _vp, _vp,
                                 C.POINTER(ie_stats), _vp]
     L.ie_solve_batch.argtypes = [C.POINTER(ie_batch_item), _i32, _i32]
+    L.ie_solve_batch_fused.argtypes = [C.POINTER(ie_batch_item), _i32, _vp]
     L.ie_eig_sensitivity.argtypes = [_vp, _vp, _i64, _vp, _i64, _i32, ie_complex, _vp, _i64, _vp,
                                      _vp, _vp]
     for f in EXPORTS:
@@ -333,19 +334,17 @@ def ie_eig_sensitivity(h, X, Y, alpha=1j, S=None, gbar=None, grad=None, stream=N
                                      _stream(stream))
 
 
-def ie_solve_batch(problems, max_workers=0, streams=None):
-    """problems: list of (handle, Y0 or None, X, k). Runs their drivers concurrently
-    (ie_solve_batch). Returns (status, [dict(status, lam, rho, e, n_found, stats)])."""
+def _batch_items(problems, streams, where):
     nb = len(problems)
     items = (ie_batch_item * nb)()
     keep = []
     for i, (h, Y0, X, k) in enumerate(problems):
         p0, ld0, n0, k0 = _block(Y0)
         if Y0 is not None:
-            _check_rows(h, n0, "ie_solve_batch")
+            _check_rows(h, n0, where)
             if k0 < k:
-                raise ValueError(f"ie_solve_batch: item {i} starting block has {k0} columns")
-        px, ldx = _out_cols(h, X, k, f"ie_solve_batch item {i}")
+                raise ValueError(f"{where}: item {i} starting block has {k0} columns")
+        px, ldx = _out_cols(h, X, k, f"{where} item {i}")
         lam = np.zeros(k, dtype=np.complex128)
         rho = np.zeros(k)
         e = np.zeros(k)
@@ -361,13 +360,33 @@ def ie_solve_batch(problems, max_workers=0, streams=None):
         it.h_e = e.ctypes.data
         s_ = streams[i] if streams is not None else None
         it.stream = (s_ if isinstance(s_, int) else s_.cuda_stream) if s_ is not None else None
-    st = load().ie_solve_batch(items, nb, int(max_workers))
+    return items, keep
+
+
+def _batch_results(items, keep):
     out = []
-    for i in range(nb):
+    for i in range(len(keep)):
         lam, rho, e = keep[i]
         out.append({"status": items[i].status, "lam": lam, "rho": rho, "e": e,
                     "n_found": items[i].n_found, "stats": items[i].stats.as_dict()})
-    return st, out
+    return out
+
+
+def ie_solve_batch(problems, max_workers=0, streams=None):
+    """problems: list of (handle, Y0 or None, X, k). Runs their drivers concurrently
+    (ie_solve_batch). Returns (status, [dict(status, lam, rho, e, n_found, stats)])."""
+    items, keep = _batch_items(problems, streams, "ie_solve_batch")
+    st = load().ie_solve_batch(items, len(problems), int(max_workers))
+    return st, _batch_results(items, keep)
+
+
+def ie_solve_batch_fused(problems, stream=None):
+    """problems: list of (handle, Y0 or None, X, k). All drivers advance in lockstep with one
+    batched band-solve launch per Arnoldi step (ie_solve_batch_fused).
+    Returns (status, [dict(status, lam, rho, e, n_found, stats)])."""
+    items, keep = _batch_items(problems, None, "ie_solve_batch_fused")
+    st = load().ie_solve_batch_fused(items, len(problems), _stream(stream))
+    return st, _batch_results(items, keep)
 
 
 def ie_get_coeffs(h, p, q):

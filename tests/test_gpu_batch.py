@@ -97,3 +97,48 @@ def test_mixed_precision_batch_equals_individual_solves(ie):
     finally:
         for c in cases:
             c.close()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_fused_batch_equals_individual_solves_and_golden(ie, precision):
+    """ie_solve_batch_fused: one band-solve launch per Arnoldi step serves every problem of the
+    batch (uneven n, band, poles, block widths, odd p, both drivers). Each item matches its
+    reference eigenvalues at rho <= 1e-10 and its one-at-a-time ie_solve (complex128: the same
+    kernels in the same order per problem, so the same eigenvalues to rounding)."""
+    names = NAMES if precision == 0 else ["m1_m64", "b0_m64_d0", "b2_m96_d0", "r1_m37"]
+    cases = [Case(ie, nm, precision=precision, driver=(2 if i % 2 else 1))
+             for i, nm in enumerate(names)]
+    try:
+        probs, outs = [], []
+        for i, c in enumerate(cases):
+            k = c.w["k"]
+            X = (np.zeros((c.n, k), dtype=np.complex128, order="F") if i == 1 else dzeros(c.n, k))
+            outs.append(X)
+            probs.append((c.h, dblock(_start(c)), X, k))
+        st, res = ie.ie_solve_batch_fused(probs)
+        assert st == ie.IE_OK, [ie.ie_status_str(r["status"]) for r in res]
+        for c, r in zip(cases, res):
+            nf = r["n_found"]
+            ref = golden_eigs(c.w)
+            assert nf == len(ref), (c.w, nf)
+            match_eigs(r["lam"][:nf], ref)
+            assert np.all(r["rho"][:nf] <= 1e-10)
+            k = c.w["k"]
+            st1, lam1, _, _, nf1, _ = ie.ie_solve(c.h, dblock(_start(c)), dzeros(c.n, k), k)
+            assert st1 == ie.IE_OK and nf1 == nf
+            assert np.max(np.abs(lam1[:nf] - r["lam"][:nf]) / np.abs(lam1[:nf])) < 1e-11
+    finally:
+        for c in cases:
+            c.close()
+
+
+def test_fused_batch_rejects_shared_handles_and_empty(ie):
+    c = Case(ie, "c1_m24")
+    try:
+        k = c.w["k"]
+        st, _ = ie.ie_solve_batch_fused([(c.h, None, dzeros(c.n, k), k), (c.h, None, dzeros(c.n, k), k)])
+        assert st == ie.IE_ERR_ARG
+        st, _ = ie.ie_solve_batch_fused([])
+        assert st == ie.IE_ERR_ARG
+    finally:
+        c.close()
