@@ -355,6 +355,303 @@ __global__ void __launch_bounds__(512) band_lu_kernel(int64_t n, int kl, int lda
   }
 }
 
+// ----------------------------------------------------------------------------------------------
+// Blocked form of the same factorisation: panels of LNB = 16 columns. CTA b of a pole owns the
+// column blocks K with K % P == b. The owner of panel J factors it on a register tile (rows
+// J*LNB .. J*LNB + LNB - 1 + kl, the panel's LNB columns) with barriers of its own CTA only,
+// and publishes the panel's multipliers, pivot offsets and column extent ju in a per-pole ring
+// slot (release flag, as above). Every CTA then applies panel J to each of its blocks in reach
+// (columns up to ju) on a register tile of the same rows: the panel's LNB steps (row swap,
+// then rank-1 elimination) in gbtf2's order, one barrier per step; a block is loaded from the
+// band storage once per panel and written back once. Look-ahead: the owner of block J+1
+// applies panel J to it first, factors it and publishes panel J+1 before its other blocks.
+// Every element receives exactly the operations of band_lu_kernel in the same order (steps
+// that gbtf2 skips for a column beyond ju act on exact zeros and leave it unchanged), so the
+// factors are identical; only the synchronisation differs: one flag per 16 columns instead of
+// one per column, and the column block stays on chip for the 16 steps.
+constexpr int LNB = 16;        // panel width
+constexpr int LTR = 128;       // row lanes of a tile (threads tid & 127)
+constexpr int LRPT = 5;        // rows per thread at most: tiles up to 640 rows (kl <= 624)
+
+template <typename CT, int RPT>
+struct LuTile {
+  CT v[RPT][LNB / 4];
+};
+
+// RPT: tile rows per thread (3 for tiles of <= 384 rows, 5 up to 640)
+template <typename CT, int RPT>
+__global__ void __launch_bounds__(512, 1) band_lu_blocked_kernel(
+    int64_t n, int kl, int ldab, int64_t n_pad, CT* AB, int* piv, CT* dinv, CT* ring,
+    int* ring_tp, unsigned* ring_flag, int R, int* status, int P, int64_t skip_publish) {
+  using RT = decltype(lu_abs1(CT{}));
+  const int pole = blockIdx.x / P, b = blockIdx.x % P;
+  const int tid = threadIdx.x, tx = tid & (LTR - 1), ty = tid >> 7;   // 4 column groups
+  const int kv = 2 * kl;
+  const int RTL = LNB + kl;                 // tile rows
+  const int64_t npan = (n + LNB - 1) / LNB;
+  CT* A = AB + (int64_t)pole * n_pad * ldab;
+  int* pv_out = piv + (int64_t)pole * n_pad;
+  CT* di_out = dinv + (int64_t)pole * n_pad;
+  // ring slot: LNB columns of kl multipliers, then (in ring_tp) LNB pivot offsets + ju
+  CT* rmul = ring + (int64_t)pole * R * LNB * kl;
+  int* rtp = ring_tp + (int64_t)pole * R * (LNB + 1);
+  unsigned* rflag = ring_flag + (int64_t)pole * R;
+  extern __shared__ __align__(16) unsigned char lu_sm_raw[];
+  CT* msm = (CT*)lu_sm_raw;                 // [LNB][kl]: staged multipliers of the applied panel
+  CT* ubuf = msm + (size_t)LNB * kl;        // [2][LNB]: pivot row after the swap
+  CT* wbuf = ubuf + 2 * LNB;                // [2][LNB]: old row j (goes to the pivot row)
+  CT* mcol = wbuf + 2 * LNB;                // [2][RTL]: multipliers of the current factor step
+  __shared__ int s_tp[LNB + 1];
+  __shared__ RT red_v[4];
+  __shared__ int red_i[4];
+
+  auto stor = [&](int64_t r, int64_t c) -> bool {   // (r, c) inside the band storage
+    return c < n && r < n && r >= c - kv && r <= c + kl;
+  };
+  auto load_tile = [&](int64_t J, int64_t K, LuTile<CT, RPT>& t) {
+#pragma unroll
+    for (int i = 0; i < RPT; ++i) {
+      const int rr = tx + i * LTR;
+      const int64_t r = J * LNB + rr;
+#pragma unroll
+      for (int q = 0; q < LNB / 4; ++q) {
+        const int64_t c = K * LNB + ty * (LNB / 4) + q;
+        t.v[i][q] = (rr < RTL && stor(r, c)) ? A[c * ldab + kv + (r - c)] : lu_zero<CT>();
+      }
+    }
+  };
+  auto store_tile = [&](int64_t J, int64_t K, const LuTile<CT, RPT>& t) {
+#pragma unroll
+    for (int i = 0; i < RPT; ++i) {
+      const int rr = tx + i * LTR;
+      const int64_t r = J * LNB + rr;
+#pragma unroll
+      for (int q = 0; q < LNB / 4; ++q) {
+        const int64_t c = K * LNB + ty * (LNB / 4) + q;
+        if (rr < RTL && stor(r, c)) A[c * ldab + kv + (r - c)] = t.v[i][q];
+      }
+    }
+  };
+  // steps of panel J (multipliers in msm, offsets in s_tp) on block K's tile
+  auto apply_panel = [&](int64_t J, LuTile<CT, RPT>& t) {
+    const int nst = (int)((n - J * LNB) < LNB ? (n - J * LNB) : LNB);
+    for (int jj = 0; jj < nst; ++jj) {
+      const int tp = s_tp[jj];
+      const int buf = jj & 1;
+      // rows j = jj and p = jj + tp of the tile publish their values
+#pragma unroll
+      for (int i = 0; i < RPT; ++i) {
+        const int rr = tx + i * LTR;
+#pragma unroll
+        for (int q = 0; q < LNB / 4; ++q) {
+          if (rr == jj) wbuf[buf * LNB + ty * (LNB / 4) + q] = t.v[i][q];
+          if (rr == jj + tp) ubuf[buf * LNB + ty * (LNB / 4) + q] = t.v[i][q];
+        }
+      }
+      __syncthreads();
+      const CT* m = msm + (size_t)jj * kl;   // m[t - 1]: multiplier of row j + t
+#pragma unroll
+      for (int i = 0; i < RPT; ++i) {
+        const int rr = tx + i * LTR;
+        const int d = rr - jj;
+#pragma unroll
+        for (int q = 0; q < LNB / 4; ++q) {
+          const int cc = ty * (LNB / 4) + q;
+          const CT u = ubuf[buf * LNB + cc];
+          if (d == 0) {
+            t.v[i][q] = u;
+          } else if (d > 0 && d <= kl) {
+            const CT base = (d == tp) ? wbuf[buf * LNB + cc] : t.v[i][q];
+            t.v[i][q] = lu_fms(m[d - 1], u, base);
+          }
+        }
+      }
+    }
+    __syncthreads();
+  };
+  // factor panel J on its tile: pivot search, swap (panel columns >= jj), multipliers,
+  // elimination of the panel columns > jj; results in the tile; piv/dinv written
+  // ju_init: gbtf2's running column extent after the previous panel (ju never decreases)
+  auto factor_panel = [&](int64_t J, LuTile<CT, RPT>& t, int64_t ju_init, int* ju_out) {
+    const int nst = (int)((n - J * LNB) < LNB ? (n - J * LNB) : LNB);
+    int64_t ju = ju_init;
+    for (int jj = 0; jj < nst; ++jj) {
+      const int64_t j = J * LNB + jj;
+      const int nr = (int)((n - 1 - j) < (int64_t)kl ? (n - 1 - j) : (int64_t)kl);
+      const int buf = jj & 1;
+      // pivot search over column jj, tile rows jj..jj+nr (first max of |re| + |im|)
+      const int gq = jj / (LNB / 4), qq = jj - gq * (LNB / 4);
+      if (ty == gq) {
+        RT best = -1;
+        int bi = 0;
+#pragma unroll
+        for (int i = 0; i < RPT; ++i) {
+          const int rr = tx + i * LTR;
+          const int d = rr - jj;
+          if (d >= 0 && d <= nr) {
+            RT a_ = 0;
+#pragma unroll
+            for (int q = 0; q < LNB / 4; ++q)
+              if (q == qq) a_ = lu_abs1(t.v[i][q]);
+            if (a_ > best || (a_ == best && d < bi)) { best = a_; bi = d; }
+          }
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+          const RT ob = __shfl_xor_sync(0xffffffffu, best, o);
+          const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+          if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+        }
+        if ((tx & 31) == 0) { red_v[tx >> 5] = best; red_i[tx >> 5] = bi; }
+      }
+      __syncthreads();
+      if (tid == 0) {
+        RT bb = red_v[0];
+        int ii = red_i[0];
+        for (int w = 1; w < 4; ++w)
+          if (red_v[w] > bb || (red_v[w] == bb && red_i[w] < ii)) { bb = red_v[w]; ii = red_i[w]; }
+        s_tp[jj] = ii;
+      }
+      __syncthreads();
+      const int tp = s_tp[jj];
+      { const int64_t cand = (j + kl + tp < n - 1) ? (j + kl + tp) : (n - 1); if (cand > ju) ju = cand; }
+      // rows j and p publish their values of the panel columns >= jj
+#pragma unroll
+      for (int i = 0; i < RPT; ++i) {
+        const int rr = tx + i * LTR;
+#pragma unroll
+        for (int q = 0; q < LNB / 4; ++q) {
+          const int cc = ty * (LNB / 4) + q;
+          if (cc < jj) continue;
+          if (rr == jj) wbuf[buf * LNB + cc] = t.v[i][q];
+          if (rr == jj + tp) ubuf[buf * LNB + cc] = t.v[i][q];
+        }
+      }
+      __syncthreads();
+      const CT pvv = ubuf[buf * LNB + jj];
+      const bool zero = (pvv.x == 0 && pvv.y == 0);
+      const CT rcp = zero ? lu_zero<CT>() : lu_rcp(pvv);
+      // column jj: the swap and the multipliers (kept in the tile as L, and in mcol)
+      if (ty == gq) {
+#pragma unroll
+        for (int i = 0; i < RPT; ++i) {
+          const int rr = tx + i * LTR;
+          const int d = rr - jj;
+#pragma unroll
+          for (int q = 0; q < LNB / 4; ++q) {
+            if (q != qq) continue;
+            if (d == 0) {
+              t.v[i][q] = pvv;
+            } else if (d > 0 && d <= nr) {
+              const CT m = zero ? lu_zero<CT>() : lu_mul((d == tp) ? wbuf[buf * LNB + jj] : t.v[i][q], rcp);
+              t.v[i][q] = m;
+              mcol[buf * RTL + rr] = m;
+            }
+          }
+        }
+      }
+      if (tid == 0) {
+        if (zero) atomicMax(status + ST_SINGULAR, 1);
+        pv_out[j] = (int)(j + tp);
+        di_out[j] = rcp;
+      }
+      __syncthreads();
+      // elimination of the panel columns > jj
+#pragma unroll
+      for (int i = 0; i < RPT; ++i) {
+        const int rr = tx + i * LTR;
+        const int d = rr - jj;
+#pragma unroll
+        for (int q = 0; q < LNB / 4; ++q) {
+          const int cc = ty * (LNB / 4) + q;
+          if (cc <= jj) continue;
+          const CT u = ubuf[buf * LNB + cc];
+          if (d == 0) {
+            t.v[i][q] = u;
+          } else if (d > 0 && d <= nr) {
+            const CT base = (d == tp) ? wbuf[buf * LNB + cc] : t.v[i][q];
+            t.v[i][q] = lu_fms(mcol[buf * RTL + rr], u, base);
+          }
+        }
+      }
+    }
+    __syncthreads();
+    *ju_out = (int)ju;
+  };
+  // publish panel J: multipliers of each column (from the tile), offsets, ju; then the flag
+  auto publish = [&](int64_t J, const LuTile<CT, RPT>& t, int ju) {
+    const int nst = (int)((n - J * LNB) < LNB ? (n - J * LNB) : LNB);
+    CT* slot = rmul + (J % R) * LNB * kl;
+#pragma unroll
+    for (int i = 0; i < RPT; ++i) {
+      const int rr = tx + i * LTR;
+#pragma unroll
+      for (int q = 0; q < LNB / 4; ++q) {
+        const int cc = ty * (LNB / 4) + q;
+        const int d = rr - cc;
+        if (cc < nst && d >= 1 && d <= kl) slot[(size_t)cc * kl + d - 1] = t.v[i][q];
+      }
+    }
+    if (tid < LNB) rtp[(J % R) * (LNB + 1) + tid] = s_tp[tid];
+    if (tid == 0) rtp[(J % R) * (LNB + 1) + LNB] = ju;
+    __syncthreads();
+    if (tid == 0 && J != skip_publish) {   // skip_publish: failure test hook (normally -1)
+      __threadfence();
+      st_release_u32(rflag + (J % R), (unsigned)(J + 1));
+    }
+  };
+  auto owner = [&](int64_t K) { return (int)(K % P); };
+
+  LuTile<CT, RPT> tile;
+  if (npan > 0 && owner(0) == b) {
+    int ju;
+    load_tile(0, 0, tile);
+    factor_panel(0, tile, 0, &ju);
+    store_tile(0, 0, tile);
+    publish(0, tile, ju);
+  }
+  for (int64_t J = 0; J < npan; ++J) {
+    if (!lu_wait_flag(rflag + (J % R), (unsigned)(J + 1), status)) return;
+    // stage panel J: multipliers, offsets, column extent
+    const CT* slot = rmul + (J % R) * LNB * kl;
+    for (int e = tid; e < LNB * kl; e += blockDim.x) msm[e] = __ldcg(slot + e);
+    if (tid <= LNB) s_tp[tid] = __ldcg(rtp + (J % R) * (LNB + 1) + tid);
+    __syncthreads();
+    const int64_t ju = s_tp[LNB];
+    const int64_t kmax = ju / LNB < npan - 1 ? ju / LNB : npan - 1;
+    // look-ahead: block J+1 first, then its factorisation and publication
+    const bool own_next = J + 1 < npan && owner(J + 1) == b;
+    if (own_next) {
+      int jun;
+      load_tile(J, J + 1, tile);
+      apply_panel(J, tile);
+      store_tile(J, J + 1, tile);
+      __syncthreads();
+      // panel J+1's tile starts one panel lower: reload it from the band storage
+      load_tile(J + 1, J + 1, tile);
+      factor_panel(J + 1, tile, ju, &jun);
+      store_tile(J + 1, J + 1, tile);
+      publish(J + 1, tile, jun);
+      // the staged panel J was overwritten by s_tp of panel J+1: restore the offsets
+      if (tid <= LNB) s_tp[tid] = __ldcg(rtp + (J % R) * (LNB + 1) + tid);
+      __syncthreads();
+    }
+    for (int64_t K = J + 1 + (own_next ? 1 : 0); K <= kmax; ++K) {
+      if (owner(K) != b) continue;
+      load_tile(J, K, tile);
+      apply_panel(J, tile);
+      store_tile(J, K, tile);
+    }
+    __syncthreads();
+  }
+}
+
+// Ring storage a pole needs: multipliers (elements of the factor type) and offsets (ints).
+size_t band_lu_ring_elems(int q, int kl) {
+  const size_t R = (size_t)band_lu_ring_slots(q);
+  return (size_t)q * R * (size_t)LNB * (size_t)(kl + 1);
+}
+size_t band_lu_ring_ints(int q) { return (size_t)q * (size_t)band_lu_ring_slots(q) * (LNB + 1); }
+
 int band_lu_ring_slots(int q) {
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
@@ -363,10 +660,53 @@ int band_lu_ring_slots(int q) {
   return 2 * (pmax > 1 ? pmax : 1) + 2;
 }
 
+// IE_LU_BLOCKED=0 in the environment selects the column-by-column kernel (the same factors).
+static bool lu_blocked_enabled() {
+  static const bool on = [] {
+    const char* e = getenv("IE_LU_BLOCKED");
+    return !(e && e[0] == '0');
+  }();
+  return on;
+}
+
+template <typename CT>
+static cudaError_t band_lu_blocked_t(int q, int64_t n, int kl, int ldab, int64_t n_pad, CT* AB,
+                                     int* piv, CT* dinv, CT* ring, int* ring_tp,
+                                     unsigned* ring_flag, int R, int* status, cudaStream_t s,
+                                     int* ctas_per_pole) {
+  int dev = 0, sms = 0, per_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int kv = 2 * kl;
+  int P = sms / q;
+  if (P > kv / LNB + 2) P = kv / LNB + 2;   // blocks one panel can reach, plus the next panel
+  if (P > R - 2) P = R - 2;                 // ring slots outlive the CTAs' spread (see above)
+  if (P < 1) return cudaErrorInvalidValue;
+  const size_t smem = ((size_t)LNB * kl + 4 * LNB + 2 * (LNB + kl)) * sizeof(CT);
+  auto kfn = (LNB + kl <= 3 * LTR) ? band_lu_blocked_kernel<CT, 3> : band_lu_blocked_kernel<CT, 5>;
+  ie_smem_optin((const void*)kfn);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kfn, 512, smem);
+  if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  while ((int64_t)P * q > (int64_t)per_sm * sms && P > 1) --P;
+  if (ctas_per_pole) *ctas_per_pole = P;
+  cudaMemsetAsync(ring_flag, 0, sizeof(unsigned) * (size_t)R * q, s);
+  // Failure test hook: IE_TEST_SKIP_PUBLISH=J makes the owner of panel J never set its flag
+  // (every wait for that panel runs out after IE_WAIT_NS; ie_create reports IE_ERR_TIMEOUT).
+  int64_t skip_publish = -1;
+  if (const char* e = getenv("IE_TEST_SKIP_PUBLISH")) skip_publish = atoll(e);
+  void* args[] = {&n, &kl, &ldab, &n_pad, &AB, &piv, &dinv, &ring, &ring_tp, &ring_flag, &R,
+                  &status, &P, &skip_publish};
+  ie_count_launch();
+  return cudaLaunchCooperativeKernel((void*)kfn, dim3(q * P), dim3(512), args, smem, s);
+}
+
 template <typename CT>
 static cudaError_t band_lu_t(int q, int64_t n, int kl, int ldab, int64_t n_pad, CT* AB, int* piv,
                              CT* dinv, CT* ring, int* ring_tp, unsigned* ring_flag, int R,
                              int* status, cudaStream_t s, int* ctas_per_pole) {
+  if (lu_blocked_enabled() && LNB + kl <= LTR * LRPT)
+    return band_lu_blocked_t(q, n, kl, ldab, n_pad, AB, piv, dinv, ring, ring_tp, ring_flag, R,
+                             status, s, ctas_per_pole);
   int dev = 0, sms = 0, per_sm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);

@@ -473,8 +473,8 @@ extern "C" ie_status ie_create(const ie_pencil* pen, ie_complex center, double r
       h->alloc(&h->piv, (size_t)q * h->n_pad) != cudaSuccess ||
       (mixed ? h->alloc(&h->dinv32, (size_t)q * h->n_pad)
              : h->alloc(&h->dinv, (size_t)q * h->n_pad)) != cudaSuccess ||
-      h->alloc(&h->lu_ring, (size_t)q * band_lu_ring_slots(q) * (kl + 1)) != cudaSuccess ||
-      h->alloc(&h->lu_ring_tp, (size_t)q * band_lu_ring_slots(q)) != cudaSuccess ||
+      h->alloc(&h->lu_ring, band_lu_ring_elems(q, kl)) != cudaSuccess ||
+      h->alloc(&h->lu_ring_tp, band_lu_ring_ints(q)) != cudaSuccess ||
       h->alloc(&h->bar, (size_t)q * band_lu_ring_slots(q)) != cudaSuccess ||
       h->alloc(&h->status, ST_COUNT) != cudaSuccess)
     return fail(IE_ERR_OOM);

@@ -109,6 +109,10 @@ void launch_assemble(const DiaDev& P, const cplx* d_poles, int q, int kl, int ld
 // Batched band LU with partial pivoting, all q poles in one cooperative launch.
 // Ring slots per pole for the LU's published pivots (> the CTAs per pole it will use).
 int band_lu_ring_slots(int q);
+// sizes of the LU's publication ring for q poles: multiplier elements (of the factor type,
+// allocated as complex128 they cover either precision) and int offsets
+size_t band_lu_ring_elems(int q, int kl);
+size_t band_lu_ring_ints(int q);
 cudaError_t launch_band_lu(int q, int64_t n, int kl, int ldab, int64_t n_pad, cplx* AB,
                            int* piv, cplx* dinv, cplx* ring, int* ring_tp, unsigned* ring_flag,
                            int R, int* status, cudaStream_t s, int* ctas_per_pole);
