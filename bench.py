@@ -36,11 +36,12 @@ HBM_FALLBACK_GBS = 6800.0
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12     # 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # 152 SMs x 128 FP32 FMA/clk x 2 flop x 2.07 GHz
 # DRAM traffic of one complex128 band_solve_kernel launch per algorithmic byte, from the ncu
-# capture at p1_m160 (profiles/band_solve_blocked_c128_p1_m160.md): dram__bytes_read.sum +
-# dram__bytes_write.sum = 1.938303e9 + 0.399454e9 B against 2.231832e9 algorithmic bytes. The
-# traffic is the factors (q n (kl + kv) entries, once) plus the blocks, so it scales with the
-# algorithmic bytes; the bench workload's traffic is this ratio times its algorithmic bytes.
-C128_SOLVE_TRAFFIC_RATIO = (1.938303e9 + 0.399454e9) / 2.231832e9
+# capture at p1_m160 (profiles/band_solve_blocked_c128_p1_m160.md, the current kernel):
+# dram__bytes_read.sum + dram__bytes_write.sum = 1.933231e9 + 0.399216e9 B against 2.231832e9
+# algorithmic bytes. The traffic is the factors (q n (kl + kv) entries, once) plus the blocks,
+# so it scales with the algorithmic bytes; the bench workload's traffic is this ratio times its
+# algorithmic bytes.
+C128_SOLVE_TRAFFIC_RATIO = (1.933231e9 + 0.399216e9) / 2.231832e9
 
 
 def parse():

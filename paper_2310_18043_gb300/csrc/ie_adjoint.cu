@@ -229,7 +229,8 @@ __global__ void __maxnreg__(REGS) band_solve_adj_kernel(AdjArgsT<CT> a) {
   CT* xs = hd + NB * NC;                                       // [NB][NC] solved head
   CT* hv = xs + NB * NC;                                       // [16][NC] members
   CT* dv = hv + 16 * NC;                                       // [NB][NC] dot inputs
-  CT* win = dv + NB * NC;                                      // [S2][NC] phase-2 window
+  CT* part = dv + NB * NC;                                     // [NPART][NB][NC] partials
+  CT* win = part + NPART * NB * NC;                            // [S2][NC] phase-2 window
   unsigned char* mflag = (unsigned char*)(win + (size_t)S2 * NC);   // [S2] member marks
   unsigned char* stage0 = (unsigned char*)(((uintptr_t)(mflag + S2) + 127) & ~(uintptr_t)127);
   const size_t p1_cols = (size_t)NB * kvp * sizeof(CT);
@@ -269,8 +270,11 @@ __global__ void __maxnreg__(REGS) band_solve_adj_kernel(AdjArgsT<CT> a) {
   for (int i = tid; i < S2; i += T) mflag[i] = 0;
 
   // ------------------------------- phase 1: U^H w = rhs ---------------------------------------
-  // Block = panel P, head rows j0..j0+7; window of Sf = kv + NB rows j0..j0+Sf-1 (slot = row
-  // mod Sf). Stage: U rows j0..j0+7 (contiguous) and the panel's inverse diagonal block.
+  // Block = panel P, head rows j0..j0+7 in hd (shared memory); the register window holds the
+  // rows the panel updates, j0+8..j0+7+kv, Sf = max(kv, NB) slots (slot = (row - NB) mod Sf).
+  // After the update the window's first NB rows become the next head and their slots take
+  // the rows entering the window. Stage: U rows j0..j0+7 (contiguous) and the panel's
+  // inverse diagonal block.
   auto issue1 = [&](int64_t P, int st) {
     unsigned char* dst = stage0 + (size_t)st * stage_bytes;
     const uint32_t bar = smem_u32(&mbar[st]);
@@ -278,23 +282,25 @@ __global__ void __maxnreg__(REGS) band_solve_adj_kernel(AdjArgsT<CT> a) {
     bulk_g2s(smem_u32(dst), Utp + P * NB * a.ldu, (uint32_t)p1_cols, bar);
     bulk_g2s(smem_u32(dst + p1_cols), Uip + P * 64, (uint32_t)(64 * sizeof(CT)), bar);
   };
-  const int Sf = kv + NB;
+  const int Sf = kv > NB ? kv : NB;
   CT v[SPT][NC], nxt[SPT][NC];
   int64_t row[SPT];
-  if (tid == 0)
+  if (tid == T - 32)
     for (int st = 0; st < a.nstage && st < npanel; ++st) issue1(st, st);
+  for (int e = tid; e < NB * NC; e += T) {
+    const int t = e / NC, c = e - (e / NC) * NC;
+    hd[e] = (t < n && c < ncol) ? R[(int64_t)(c0 + c) * a.ldr + t] : zero;
+  }
 #pragma unroll
   for (int u = 0; u < SPT; ++u) {
     const int s = tid + u * T;
-    row[u] = s;
+    const int64_t r = NB + s;
+    row[u] = r;
 #pragma unroll
     for (int c = 0; c < NC; ++c) {
-      v[u][c] = (s < Sf && s < n && c < ncol) ? R[(int64_t)(c0 + c) * a.ldr + s] : zero;
-      nxt[u][c] = (s < Sf && s + Sf < n && c < ncol) ? R[(int64_t)(c0 + c) * a.ldr + s + Sf] : zero;
+      v[u][c] = (s < Sf && r < n && c < ncol) ? R[(int64_t)(c0 + c) * a.ldr + r] : zero;
+      nxt[u][c] = (s < Sf && r + Sf < n && c < ncol) ? R[(int64_t)(c0 + c) * a.ldr + r + Sf] : zero;
     }
-    if (s < Sf && s < NB)
-#pragma unroll
-      for (int c = 0; c < NC; ++c) hd[s * NC + c] = v[u][c];
   }
   __syncthreads();
   bool failed = false;
@@ -303,19 +309,45 @@ __global__ void __maxnreg__(REGS) band_solve_adj_kernel(AdjArgsT<CT> a) {
     if (!mbar_wait_bounded(smem_u32(&mbar[st]), (uint32_t)((P / a.nstage) & 1))) s_fail = 1;
     __syncthreads();
     if (s_fail) { failed = true; break; }
-    // the previous panel's stage is free: refill it
-    if (tid == 0 && P >= 1 && P - 1 + a.nstage < npanel)
+    // the previous panel's stage is free: refill it (the last warp issues the copies)
+    if (tid == T - 32 && P >= 1 && P - 1 + a.nstage < npanel)
       issue1(P - 1 + a.nstage, (int)((P - 1) % a.nstage));
     const CT* Ust = (const CT*)(stage0 + (size_t)st * stage_bytes);
     const CT* Uist = (const CT*)(stage0 + (size_t)st * stage_bytes + p1_cols);
     const int64_t j0 = P * NB;
-    // head block: U_blk^H w_h = h, w_h[t] = sum_s conj(inv(U_blk)[s][t]) h[s]
-    for (int e = tid; e < NB * NC; e += T) {
+    // head block: U_blk^H w_h = h, w_h[t] = sum_s conj(inv(U_blk)[s][t]) h[s], in NPART fixed
+    // partial ranges of s (FP64: one warp each, then a barrier; FP32: all in one thread); the
+    // head rows leave with w
+    auto head_out = [&](int e, CT acc) {
       const int t = e / NC, c = e - (e / NC) * NC;
-      CT acc = zero;
-#pragma unroll
-      for (int s2 = 0; s2 < NB; ++s2) acc = cfma_conj(Uist[s2 * NB + t], hd[s2 * NC + c], acc);
       xs[e] = acc;
+      if (j0 + t < n && c < ncol) Yo[(int64_t)(c0 + c) * a.ldy + j0 + t] = acc;
+    };
+    if constexpr (sizeof(CT) == sizeof(float2)) {
+      for (int e = tid; e < NB * NC; e += T) {
+        const int t = e / NC, c = e - (e / NC) * NC;
+        CT p[NPART];
+#pragma unroll
+        for (int g = 0; g < NPART; ++g) {
+          p[g] = zero;
+#pragma unroll
+          for (int s2 = 2 * g; s2 < 2 * g + 2; ++s2)
+            p[g] = cfma_conj(Uist[s2 * NB + t], hd[s2 * NC + c], p[g]);
+        }
+        head_out(e, sum_parts(p, 1, 0));
+      }
+    } else {
+      for (int e = tid; e < NPART * NB * NC; e += T) {
+        const int g = e / (NB * NC), o = e - g * (NB * NC);
+        const int t = o / NC, c = o - (o / NC) * NC;
+        CT acc = zero;
+#pragma unroll
+        for (int s2 = 2 * g; s2 < 2 * g + 2; ++s2)
+          acc = cfma_conj(Uist[s2 * NB + t], hd[s2 * NC + c], acc);
+        part[e] = acc;
+      }
+      __syncthreads();
+      for (int e = tid; e < NB * NC; e += T) head_out(e, sum_parts(part, NB * NC, e));
     }
     __syncthreads();
 #pragma unroll
@@ -323,12 +355,21 @@ __global__ void __maxnreg__(REGS) band_solve_adj_kernel(AdjArgsT<CT> a) {
       const int s = tid + u * T;
       if (s >= Sf) continue;
       const int64_t r = row[u];
-      if (r < j0 + NB) {
-        const int t = (int)(r - j0);
-        if (r < n)
+      const int base = (int)(r - j0);            // >= NB for every window row
 #pragma unroll
-          for (int c = 0; c < NC; ++c)
-            if (c < ncol) Yo[(int64_t)(c0 + c) * a.ldy + r] = xs[t * NC + c];
+      for (int jj = 0; jj < NB; ++jj) {
+        const int d = base - jj;
+        if (d <= kv) {
+          const CT uu = Ust[(size_t)jj * kvp + d - 1];
+#pragma unroll
+          for (int c = 0; c < NC; ++c) v[u][c] = cfms_conj(uu, xs[jj * NC + c], v[u][c]);
+        }
+      }
+      // rows j0+NB..j0+2NB-1 are the next panel's head: to hd, and the slot takes row r + Sf
+      const int dh = base - NB;
+      if (dh < NB) {
+#pragma unroll
+        for (int c = 0; c < NC; ++c) hd[dh * NC + c] = v[u][c];
         const int64_t r2 = r + Sf;
         row[u] = r2;
 #pragma unroll
@@ -336,25 +377,6 @@ __global__ void __maxnreg__(REGS) band_solve_adj_kernel(AdjArgsT<CT> a) {
           v[u][c] = nxt[u][c];
           nxt[u][c] = (r2 + Sf < n && c < ncol) ? R[(int64_t)(c0 + c) * a.ldr + r2 + Sf] : zero;
         }
-        // a refilled row lies beyond this block's band; with kv < NB it is already a head
-        // row of the next block
-        if (r2 < j0 + 2 * NB)
-#pragma unroll
-          for (int c = 0; c < NC; ++c) hd[(int)(r2 - j0 - NB) * NC + c] = v[u][c];
-      } else {
-        const int base = (int)(r - j0);
-#pragma unroll
-        for (int jj = 0; jj < NB; ++jj) {
-          const int d = base - jj;
-          if (d >= 1 && d <= kv) {
-            const CT uu = Ust[(size_t)jj * kvp + d - 1];
-#pragma unroll
-            for (int c = 0; c < NC; ++c) v[u][c] = cfms_conj(uu, xs[jj * NC + c], v[u][c]);
-          }
-        }
-        if (r < j0 + 2 * NB)
-#pragma unroll
-          for (int c = 0; c < NC; ++c) hd[(int)(r - j0 - NB) * NC + c] = v[u][c];
       }
     }
     __syncthreads();
@@ -538,7 +560,7 @@ static cudaError_t launch_adj(AdjArgsT<CT> a, int q, cudaStream_t s) {
   int nc = ncmax;
   for (int c = 1; c <= ncmax; c *= 2)
     if ((int64_t)q * ((a.k + c - 1) / c) <= sms) { nc = c; break; }
-  const int slots = a.kv + NB;
+  const int slots = a.kv > NB ? a.kv : NB;   // phase-1 window (head rows in shared memory)
   const int spt = (slots > 576) ? 2 : 1;
   // two slots per thread with the widest column groups spill registers
   if (spt == 2) nc = std::min(nc, fp32 ? 4 : 2);
@@ -549,7 +571,8 @@ static cudaError_t launch_adj(AdjArgsT<CT> a, int q, cudaStream_t s) {
   const size_t stage_bytes = ((p1 > p2 ? p1 : p2) + 127) & ~(size_t)127;
   const size_t budget = 224 * 1024;   // below the 227 KB per-block opt-in limit
   auto fixed_for = [&](int c) {
-    return 128 + (size_t)(3 * NB + 16) * c * sizeof(CT) + (size_t)(a.kl + NB) * c * sizeof(CT) +
+    return 128 + (size_t)(3 * NB + 16 + NPART * NB) * c * sizeof(CT) +
+           (size_t)(a.kl + NB) * c * sizeof(CT) +
            (size_t)(a.kl + NB) + 256;
   };
   while (nc > 1 && fixed_for(nc) + 2 * stage_bytes > budget) nc >>= 1;

@@ -69,4 +69,25 @@ __device__ __forceinline__ double2 cfms_conj(double2 a, double2 b, double2 c) {
 }
 __device__ __forceinline__ double2 to_d(double2 v) { return v; }
 __device__ __forceinline__ double2 to_d(float2 v) { return make_double2(v.x, v.y); }
+
+// The short dense products of a panel -- H <- T H over the 16 members (forward) and
+// x_head = inv(U_block) h_head over the NB head rows (backward) -- are summed in four fixed
+// partial ranges (members 4g..4g+3, head rows 2g..2g+1), then the partials are added in a
+// fixed order. The synchronised kernels compute the four partials on four different warps in FP64
+// (one per SM sub-partition), one thread computes all four otherwise; the order of every
+// floating-point operation is the same either way, so every launch shape gives identical
+// results. (The conjugate-transpose solve uses the same split for its U^H head block.)
+constexpr int NPART = 4;
+template <typename CT>
+__device__ __forceinline__ CT sum_parts(const CT* part, int stride, int o) {
+  CT s = part[o];
+#pragma unroll
+  for (int g = 1; g < NPART; ++g) {
+    const CT x = part[g * stride + o];
+    s.x += x.x;
+    s.y += x.y;
+  }
+  return s;
+}
+
 }  // namespace iebulk

@@ -31,26 +31,6 @@ namespace {
 constexpr int NB = 8;   // factor columns per staged panel = backward block
 }  // namespace
 
-// The short dense products of a panel -- H <- T H over the 16 members (forward) and
-// x_head = inv(U_block) h_head over the NB head rows (backward) -- are summed in four fixed
-// partial ranges (members 4g..4g+3, head rows 2g..2g+1), then the partials are added in a
-// fixed order. The synchronised kernel computes the four partials on four different warps
-// (one per SM sub-partition), the warp-specialised kernel on one warp; the order of every
-// floating-point operation is the same in both, so every launch shape gives identical
-// results.
-constexpr int NPART = 4;
-template <typename CT>
-__device__ __forceinline__ CT sum_parts(const CT* part, int stride, int o) {
-  CT s = part[o];
-#pragma unroll
-  for (int g = 1; g < NPART; ++g) {
-    const CT x = part[g * stride + o];
-    s.x += x.x;
-    s.y += x.y;
-  }
-  return s;
-}
-
 template <typename CT>
 struct SolveArgsT {
   int64_t n, n_pad;
