@@ -317,7 +317,10 @@ ie_status ie_solve_batch(ie_batch_item* items, int32_t nb, int32_t max_workers);
  * ignored (stream is used for all). Returns IE_ERR_ARG for nb < 1, a NULL item field that
  * ie_solve requires, two items sharing a handle or a handle on another device (nothing runs);
  * otherwise IE_OK if every item returned IE_OK, else the first non-OK item status in item
- * order. Not in the paper (the paper notes disks are independent problems, Sec. 1). */
+ * order. Each item's stats carry its counters (outer iterations, n_found, GMRES steps, solve
+ * and refinement counts); its per-phase times (t_filter_ms, t_hsrr_ms) are not measured and
+ * read 0, since the phases of all items interleave. Not in the paper (the paper notes disks
+ * are independent problems, Sec. 1). */
 ie_status ie_solve_batch_fused(ie_batch_item* items, int32_t nb, void* stream);
 
 #ifdef __cplusplus

@@ -146,3 +146,23 @@ def test_mixed_every_solve_shape_matches_oracle(ie):
             assert err < 1e-11, (call, err)
     finally:
         c.close()
+
+
+def test_mixed_singular_pencil_reports_zero_pivot(ie):
+    """The complex64 blocked LU on a pencil with an exactly zero column (band 1, n not a
+    multiple of the 16-column panel): IE_ERR_SINGULAR on the host, no GPU fault, and the
+    context stays usable."""
+    n = 70
+    offsets = np.array([-1, 0, 1], dtype=np.int64)
+    A = np.zeros((3, n), dtype=np.complex128)
+    B = np.zeros((3, n), dtype=np.complex128)
+    A[1] = np.arange(1, n + 1)
+    B[1] = 1.0
+    A[1, 37] = 0.0
+    B[1, 37] = 0.0
+    st, h = ie.ie_create(n, offsets, torch.from_numpy(A).to("cuda:0"), torch.from_numpy(B).to("cuda:0"),
+                         10.0, 2.5, 4, 4, ie.ie_opts_default(k=4, precision=1))
+    assert st == ie.IE_ERR_SINGULAR
+    ie.ie_destroy(h)
+    c = mixed(ie, "c1_m24")
+    c.close()
