@@ -304,14 +304,16 @@ __global__ void __maxnreg__(REGS) band_solve_adj_kernel(AdjArgsT<CT> a) {
   }
   __syncthreads();
   bool failed = false;
-  for (int64_t P = 0; P < npanel && !failed; ++P) {
-    const int st = (int)(P % a.nstage);
-    if (!mbar_wait_bounded(smem_u32(&mbar[st]), (uint32_t)((P / a.nstage) & 1))) s_fail = 1;
+  // stage ring position and mbarrier phase as running 32-bit counters (no division per panel)
+  int st = 0, stp = a.nstage - 1;
+  uint32_t ph = 0;
+  for (int64_t P = 0; P < npanel && !failed;
+       ++P, stp = st, st = (st + 1 == a.nstage) ? 0 : st + 1, ph ^= (st == 0) ? 1u : 0u) {
+    if (!mbar_wait_bounded(smem_u32(&mbar[st]), ph)) s_fail = 1;
     __syncthreads();
     if (s_fail) { failed = true; break; }
     // the previous panel's stage is free: refill it (the last warp issues the copies)
-    if (tid == T - 32 && P >= 1 && P - 1 + a.nstage < npanel)
-      issue1(P - 1 + a.nstage, (int)((P - 1) % a.nstage));
+    if (tid == T - 32 && P >= 1 && P - 1 + a.nstage < npanel) issue1(P - 1 + a.nstage, stp);
     const CT* Ust = (const CT*)(stage0 + (size_t)st * stage_bytes);
     const CT* Uist = (const CT*)(stage0 + (size_t)st * stage_bytes + p1_cols);
     const int64_t j0 = P * NB;
@@ -437,14 +439,25 @@ __global__ void __maxnreg__(REGS) band_solve_adj_kernel(AdjArgsT<CT> a) {
   while (g > 1 && g * NB * NC > T) g >>= 1;
   const int ngroups = T / g;
   __syncthreads();
-  for (int64_t Bp = 0; Bp < npanel && !failed; ++Bp) {
+  // window slot of the panel's first row j0 = (npanel-1-Bp)*NB, kept as a running counter:
+  // slot(j0 + x) = s0 + x (- S2) for 0 <= x < 2*S2
+  int s0 = (int)(((npanel - 1) * NB) % S2);
+  auto slot = [&](int x) {
+    const int sl = s0 + x;
+    return sl >= S2 ? sl - S2 : sl;
+  };
+  st = 0;
+  stp = a.nstage - 1;
+  ph = 0;
+  for (int64_t Bp = 0; Bp < npanel && !failed;
+       ++Bp, stp = st, st = (st + 1 == a.nstage) ? 0 : st + 1, ph ^= (st == 0) ? 1u : 0u,
+               s0 = (s0 - NB < 0) ? s0 - NB + S2 : s0 - NB) {
     const int64_t P = npanel - 1 - Bp;
-    const int st = (int)(Bp % a.nstage);
-    if (!mbar_wait_bounded(smem_u32(&mbar[st]), (uint32_t)((Bp / a.nstage) & 1))) s_fail = 1;
+    if (!mbar_wait_bounded(smem_u32(&mbar[st]), ph)) s_fail = 1;
     __syncthreads();
     if (s_fail) { failed = true; break; }
     if (tid == 0 && Bp >= 1 && Bp - 1 + a.nstage < npanel)
-      issue2(npanel - 1 - (Bp - 1 + a.nstage), (int)((Bp - 1) % a.nstage));
+      issue2(npanel - 1 - (Bp - 1 + a.nstage), stp);
     const CT* Lst = (const CT*)(stage0 + (size_t)st * stage_bytes);
     const CT* Mst = (const CT*)(stage0 + (size_t)st * stage_bytes + p2_cols);
     const int* Hst = (const int*)(stage0 + (size_t)st * stage_bytes + p2_cols + 16 * MW * sizeof(CT));
@@ -454,9 +467,9 @@ __global__ void __maxnreg__(REGS) band_solve_adj_kernel(AdjArgsT<CT> a) {
     for (int e = tid; e < 16 * NC; e += T) {
       const int m = e / NC, c = e - (e / NC) * NC;
       const int hr = Hst[m];
-      hv[e] = (hr >= 0) ? win[(hr % S2) * NC + c] : zero;
+      hv[e] = (hr >= 0) ? win[slot(hr - (int)j0) * NC + c] : zero;
     }
-    if (tid < NB && Hst[NB + tid] >= 0) mflag[Hst[NB + tid] % S2] = 1;
+    if (tid < NB && Hst[NB + tid] >= 0) mflag[slot(Hst[NB + tid] - (int)j0)] = 1;
     __syncthreads();
     // (A2) d_jj = sum over non-member rows r in (j, j+kl] of conj(L(r, j)) w_r
     for (int e0 = 0; e0 < NB * NC; e0 += ngroups) {
@@ -467,7 +480,7 @@ __global__ void __maxnreg__(REGS) band_solve_adj_kernel(AdjArgsT<CT> a) {
         const int jj = e / NC, c = e - (e / NC) * NC;
         if (jj < nvalid) {
           const int64_t j = j0 + jj;
-          int sl = (int)((j + 1 + l) % S2);
+          int sl = slot(jj + 1 + l);
           for (int i = l; i < kl; i += g) {
             const int64_t r = j + 1 + i;
             if (r >= n) break;
@@ -492,9 +505,9 @@ __global__ void __maxnreg__(REGS) band_solve_adj_kernel(AdjArgsT<CT> a) {
       for (int m2 = 0; m2 < 16; ++m2) acc = cfma(Mst[m * MW + m2], hv[m2 * NC + c], acc);
 #pragma unroll
       for (int jj = 0; jj < NB; ++jj) acc = cfma(Mst[m * MW + 16 + jj], dv[jj * NC + c], acc);
-      win[(hr % S2) * NC + c] = acc;
+      win[slot(hr - (int)j0) * NC + c] = acc;
     }
-    if (tid < NB && Hst[NB + tid] >= 0) mflag[Hst[NB + tid] % S2] = 0;
+    if (tid < NB && Hst[NB + tid] >= 0) mflag[slot(Hst[NB + tid] - (int)j0)] = 0;
     __syncthreads();
     // (C) rows j0+kl .. j0+kl+7 are final: write them; rows j0-8 .. j0-1 enter their slots
 #pragma unroll
@@ -503,7 +516,7 @@ __global__ void __maxnreg__(REGS) band_solve_adj_kernel(AdjArgsT<CT> a) {
       if (e >= NB * NC) continue;
       const int t = e / NC, c = e - (e / NC) * NC;
       const int64_t r = j0 + kl + t;
-      const int sl = (int)(r % S2);
+      const int sl = slot(kl + t);
       if (r < n && c < ncol) out(r, c, win[sl * NC + c]);
       win[sl * NC + c] = pf[i];                       // row j0 - NB + t (zero if < 0)
       const int64_t r3 = j0 - 2 * NB + t;             // entering row of the next panel

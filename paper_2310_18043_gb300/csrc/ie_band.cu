@@ -223,7 +223,7 @@ __global__ void __launch_bounds__(512) band_lu_kernel(int64_t n, int kl, int lda
   // pivot search, multipliers, final column entries and publication of step jc (owner of
   // column jc only); column jc holds all updates of steps < jc in global memory
   // col[0..pre) already holds rows jc..jc+pre-1 of the column (the look-ahead update)
-  auto pivot_publish = [&](int64_t jc, int pre) {
+  auto pivot_publish = [&](int64_t jc, int pre, int jcr /* jc % R */) {
     const int nr = (int)((n - 1 - jc) < (int64_t)kl ? (n - 1 - jc) : (int64_t)kl);
     CT* cj = A + jc * ldab + kv;
     RT best = -1;
@@ -253,7 +253,7 @@ __global__ void __launch_bounds__(512) band_lu_kernel(int64_t n, int kl, int lda
     const CT pv = col[tp];
     const bool zero = (pv.x == 0 && pv.y == 0);
     const CT rcp = zero ? lu_zero<CT>() : lu_rcp(pv);
-    CT* slot = rmul + (int64_t)(jc % R) * (kl + 1);
+    CT* slot = rmul + (int64_t)jcr * (kl + 1);
     for (int t = tid; t <= nr; t += T) {
       if (t == 0) {
         cj[0] = pv;
@@ -267,28 +267,31 @@ __global__ void __launch_bounds__(512) band_lu_kernel(int64_t n, int kl, int lda
       if (zero) atomicMax(status + ST_SINGULAR, 1);
       pv_out[jc] = (int)(jc + tp);
       di_out[jc] = rcp;
-      rtp[jc % R] = tp;
+      rtp[jcr] = tp;
     }
     __syncthreads();
     if (tid == 0 && jc != skip_publish) {   // skip_publish: failure test hook (normally -1)
       __threadfence();
-      st_release_u32(rflag + (jc % R), (unsigned)(jc + 1));
+      st_release_u32(rflag + jcr, (unsigned)(jc + 1));
     }
   };
 
-  if (n > 0 && b == 0) pivot_publish(0, 0);
+  if (n > 0 && b == 0) pivot_publish(0, 0, 0);
   int64_t ju = 0;
-  for (int64_t j = 0; j < n; ++j) {
+  // jr = j % R and jp = j % P as running counters (no 64-bit division per step)
+  int jr = 0, jp = 0;
+  for (int64_t j = 0; j < n; ++j, jr = (jr + 1 == R) ? 0 : jr + 1, jp = (jp + 1 == P) ? 0 : jp + 1) {
+    const int jr1 = (jr + 1 == R) ? 0 : jr + 1, jp1 = (jp + 1 == P) ? 0 : jp + 1;
     // (a) step j's pivot offset and multipliers, published by the owner of column j
-    if (!lu_wait_flag(rflag + (j % R), (unsigned)(j + 1), status)) return;
+    if (!lu_wait_flag(rflag + jr, (unsigned)(j + 1), status)) return;
     const int nrows = (int)((n - 1 - j) < (int64_t)kl ? (n - 1 - j) : (int64_t)kl);
-    const CT* slot = rmul + (int64_t)(j % R) * (kl + 1);
+    const CT* slot = rmul + (int64_t)jr * (kl + 1);
     for (int t = 1 + tid; t <= nrows; t += T) mult[t] = __ldcg(slot + t);
-    const int tp = __ldcg(rtp + (j % R));
+    const int tp = __ldcg(rtp + jr);
     { const int64_t cand = (j + kl + tp < n - 1) ? (j + kl + tp) : (n - 1); if (cand > ju) ju = cand; }
     __syncthreads();
     // (b) look-ahead: the owner of column j+1 applies step j to it, then publishes step j+1
-    const bool own_next = (j + 1 < n) && ((j + 1) % P == b);
+    const bool own_next = (j + 1 < n) && (jp1 == b);
     if (own_next) {
       int pre = 0;
       if (j + 1 <= ju && nrows > 0) {
@@ -307,12 +310,13 @@ __global__ void __launch_bounds__(512) band_lu_kernel(int64_t n, int kl, int lda
         pre = nrows;
         __syncthreads();
       }
-      pivot_publish(j + 1, pre);
+      pivot_publish(j + 1, pre, jr1);
     }
     // (c) swap + rank-1 update of the other owned columns l in (j, ju], l % P == b
     const int64_t jn = own_next ? j + 2 : j + 1;    // column j+1 is done when owned here
-    const int64_t l0 = jn + (((int64_t)b - jn % P) % P + P) % P;
-    const int nown = (l0 <= ju && nrows >= 0) ? (int)((ju - l0) / P + 1) : 0;
+    const int jnp = own_next ? ((jp1 + 1 == P) ? 0 : jp1 + 1) : jp1;   // jn % P
+    const int64_t l0 = jn + ((b - jnp < 0) ? b - jnp + P : b - jnp);
+    const int nown = (l0 <= ju && nrows >= 0) ? (int)(ju - l0) / P + 1 : 0;
     for (int idx = tid; idx < nown; idx += T) {
       const int64_t l = l0 + (int64_t)idx * P;
       const CT* cl = A + l * ldab + kv - (l - j);     // row j of column l
@@ -609,12 +613,13 @@ __global__ void __launch_bounds__(512, 1) band_lu_blocked_kernel(
     store_tile(0, 0, tile);
     publish(0, tile, ju);
   }
-  for (int64_t J = 0; J < npan; ++J) {
-    if (!lu_wait_flag(rflag + (J % R), (unsigned)(J + 1), status)) return;
+  int Jr = 0;   // J % R, running
+  for (int64_t J = 0; J < npan; ++J, Jr = (Jr + 1 == R) ? 0 : Jr + 1) {
+    if (!lu_wait_flag(rflag + Jr, (unsigned)(J + 1), status)) return;
     // stage panel J: multipliers, offsets, column extent
-    const CT* slot = rmul + (J % R) * LNB * kl;
+    const CT* slot = rmul + (int64_t)Jr * LNB * kl;
     for (int e = tid; e < LNB * kl; e += blockDim.x) msm[e] = __ldcg(slot + e);
-    if (tid <= LNB) s_tp[tid] = __ldcg(rtp + (J % R) * (LNB + 1) + tid);
+    if (tid <= LNB) s_tp[tid] = __ldcg(rtp + Jr * (LNB + 1) + tid);
     __syncthreads();
     const int64_t ju = s_tp[LNB];
     const int64_t kmax = ju / LNB < npan - 1 ? ju / LNB : npan - 1;
@@ -632,11 +637,13 @@ __global__ void __launch_bounds__(512, 1) band_lu_blocked_kernel(
       store_tile(J + 1, J + 1, tile);
       publish(J + 1, tile, jun);
       // the staged panel J was overwritten by s_tp of panel J+1: restore the offsets
-      if (tid <= LNB) s_tp[tid] = __ldcg(rtp + (J % R) * (LNB + 1) + tid);
+      if (tid <= LNB) s_tp[tid] = __ldcg(rtp + Jr * (LNB + 1) + tid);
       __syncthreads();
     }
-    for (int64_t K = J + 1 + (own_next ? 1 : 0); K <= kmax; ++K) {
-      if (owner(K) != b) continue;
+    // this CTA's blocks K in (J + own_next, kmax]: the first by one modulo, then every P-th
+    const int64_t K0 = J + 1 + (own_next ? 1 : 0);
+    const int dk = (int)(((int64_t)b - K0 % P + P) % P);
+    for (int64_t K = K0 + dk; K <= kmax; K += P) {
       load_tile(J, K, tile);
       apply_panel(J, tile);
       store_tile(J, K, tile);

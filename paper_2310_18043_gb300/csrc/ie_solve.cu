@@ -166,14 +166,18 @@ __device__ __forceinline__ void solve_cta(const SolveArgsT<CT>& a, const int pol
     }
   }
   bool failed = false;
-  for (int64_t P = 0; P < npanel && !failed; ++P) {
-    const int st = (int)(P % a.nstage);
-    if (!mbar_wait_bounded(smem_u32(&mbar[st]), (uint32_t)((P / a.nstage) & 1))) s_fail = 1;
+  // stage ring position and mbarrier phase of the current panel, kept as running 32-bit
+  // counters (a 64-bit division by the runtime stage count per panel costs more than the
+  // panel's own bookkeeping)
+  int st = 0, stp = a.nstage - 1;
+  uint32_t ph = 0;
+  for (int64_t P = 0; P < npanel && !failed;
+       ++P, stp = st, st = (st + 1 == a.nstage) ? 0 : st + 1, ph ^= (st == 0) ? 1u : 0u) {
+    if (!mbar_wait_bounded(smem_u32(&mbar[st]), ph)) s_fail = 1;
     __syncthreads();
     if (s_fail) { failed = true; break; }
     // the previous panel's stage is free: refill it
-    if (tid == issuer && P >= 1 && P - 1 + a.nstage < npanel)
-      issue_fwd(P - 1 + a.nstage, (int)((P - 1) % a.nstage));
+    if (tid == issuer && P >= 1 && P - 1 + a.nstage < npanel) issue_fwd(P - 1 + a.nstage, stp);
     const CT* Lst = (const CT*)(stage0 + (size_t)st * stage_bytes);
     const CT* Tst = (const CT*)(stage0 + (size_t)st * stage_bytes + fwd_cols_bytes);
     const int* Hst = (const int*)(stage0 + (size_t)st * stage_bytes + fwd_cols_bytes + 256 * sizeof(CT));
@@ -335,14 +339,16 @@ __device__ __forceinline__ void solve_cta(const SolveArgsT<CT>& a, const int pol
       }
     }
   }
-  for (int64_t Bp = 0; Bp < npanel && !failed; ++Bp) {
-    const int st = (int)(Bp % a.nstage);
-    if (!mbar_wait_bounded(smem_u32(&mbar[st]), (uint32_t)((Bp / a.nstage) & 1))) s_fail = 1;
+  st = 0;
+  stp = a.nstage - 1;
+  ph = 0;
+  for (int64_t Bp = 0; Bp < npanel && !failed;
+       ++Bp, stp = st, st = (st + 1 == a.nstage) ? 0 : st + 1, ph ^= (st == 0) ? 1u : 0u) {
+    if (!mbar_wait_bounded(smem_u32(&mbar[st]), ph)) s_fail = 1;
     __syncthreads();
     if (s_fail) { failed = true; break; }
     // the previous panel's stage is free: refill it
-    if (tid == issuer && Bp >= 1 && Bp - 1 + a.nstage < npanel)
-      issue_bwd(Bp - 1 + a.nstage, (int)((Bp - 1) % a.nstage));
+    if (tid == issuer && Bp >= 1 && Bp - 1 + a.nstage < npanel) issue_bwd(Bp - 1 + a.nstage, stp);
     const CT* Ust = (const CT*)(stage0 + (size_t)st * stage_bytes);
     const CT* Uist = (const CT*)(stage0 + (size_t)st * stage_bytes + bwd_cols_bytes);
     const int64_t j0 = a.n_pad - 1 - Bp * NB;
@@ -534,20 +540,25 @@ __global__ void __maxnreg__(REGS) band_solve_pipe_kernel(SolveArgsT<CT> a) {
   {
     unsigned dsz;
     asm("mov.u32 %0, %%dynamic_smem_size;" : "=r"(dsz));
-    if ((size_t)(stage0 - sm_raw) + (size_t)ns * stage_bytes > (size_t)dsz || WU < 1) {
+    if ((size_t)(stage0 - sm_raw) + (size_t)ns * stage_bytes > (size_t)dsz || WU < 1 ||
+        (ns != 2 && ns != 4)) {
       if (tid == 0) atomicExch(a.status + ST_TIMEOUT, 1);
       return;
     }
   }
-  auto FULL = [&](int64_t G) { return smem_u32(&bars[0 * ns + (int)(G % ns)]); };
-  auto EMPTY = [&](int64_t G) { return smem_u32(&bars[1 * ns + (int)(G % ns)]); };
-  auto HDF = [&](int64_t G) { return smem_u32(&bars[2 * ns + (int)(G % ns)]); };
-  auto XSF = [&](int64_t G) { return smem_u32(&bars[3 * ns + (int)(G % ns)]); };
-  auto par = [&](int64_t G) { return (uint32_t)((G / ns) & 1); };
-  auto FAC = [&](int64_t G) { return stage0 + (size_t)(G % ns) * stage_bytes; };
-  auto OUT = [&](int64_t G) { return (CT*)(stage0 + (size_t)(G % ns) * stage_bytes + fac_bytes); };
+  // ns is 2 or 4 (the host sizes it so): stage = G mod ns and phase = (G div ns) mod 2 by masks
+  // and shifts, not by a division per use
+  const int lgns = ns == 4 ? 2 : 1;
+  auto sidx = [&](int64_t G) { return (int)(G & (ns - 1)); };
+  auto FULL = [&](int64_t G) { return smem_u32(&bars[0 * ns + sidx(G)]); };
+  auto EMPTY = [&](int64_t G) { return smem_u32(&bars[1 * ns + sidx(G)]); };
+  auto HDF = [&](int64_t G) { return smem_u32(&bars[2 * ns + sidx(G)]); };
+  auto XSF = [&](int64_t G) { return smem_u32(&bars[3 * ns + sidx(G)]); };
+  auto par = [&](int64_t G) { return (uint32_t)((G >> lgns) & 1); };
+  auto FAC = [&](int64_t G) { return stage0 + (size_t)sidx(G) * stage_bytes; };
+  auto OUT = [&](int64_t G) { return (CT*)(stage0 + (size_t)sidx(G) * stage_bytes + fac_bytes); };
   auto IN = [&](int64_t G) {
-    return (CT*)(stage0 + (size_t)(G % ns) * stage_bytes + fac_bytes + io_bytes);
+    return (CT*)(stage0 + (size_t)sidx(G) * stage_bytes + fac_bytes + io_bytes);
   };
   if (tid == 0) {
     s_fail_raw = 0;
@@ -1039,9 +1050,9 @@ static bool shape_for(SolveArgsT<CT>& a, const SolveCfg& c, int* threads, size_t
     const size_t fac = ((fwdb > bwdb ? fwdb : bwdb) + 127) & ~(size_t)127;
     const size_t stage_bytes = (fac + 2 * (size_t)16 * c.nc * sizeof(CT) + 127) & ~(size_t)127;
     const size_t budget = 200 * 1024;
-    int nstage = c.stages;
-    while (nstage > 2 && ((4 * (size_t)nstage * 8 + 127) & ~(size_t)127) + nstage * stage_bytes > budget)
-      --nstage;
+    // a power of two (the kernel indexes the ring by masks): 4 stages when they fit, else 2
+    int nstage = c.stages >= 4 ? 4 : 2;
+    if (((4 * (size_t)nstage * 8 + 127) & ~(size_t)127) + nstage * stage_bytes > budget) nstage = 2;
     const size_t need = ((4 * (size_t)nstage * 8 + 127) & ~(size_t)127) + nstage * stage_bytes;
     if (need > budget) return false;
     a.nstage = nstage;
