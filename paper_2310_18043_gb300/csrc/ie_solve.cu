@@ -45,7 +45,7 @@ struct SolveArgsT {
   const CT* dinv;     // 1/u_jj, pole stride n_pad
   // per (pole, panel) block transforms (see block_transform_kernel): forward 16x16 T and its
   // member rows, backward 8x8 inverse of U's diagonal block
-  const CT* Tb;       // [pole][panel][16][16]
+  const CT* Tb;       // [pole][panel][16][16], column m of T at m*16
   const int* Hb;      // [pole][panel][16]
   const CT* Ub;       // [pole][panel][8][8]
   const cplx* weights;
@@ -73,6 +73,48 @@ struct SolveArgsT {
 // (S rows further on, not yet touched by any solved column). Keeping the head out of the
 // register window makes the thread count S / SPT (a multiple of 4 warps for kl = 256 or
 // 512), so every sub-partition of the SM gets the same share of the update.
+// Bit m set: member m of the panel's set H is present (H entry >= 0).
+__device__ __forceinline__ unsigned present_mask(const int* Hst) {
+  unsigned pres = 0;
+#pragma unroll
+  for (int m = 0; m < 16; ++m) pres |= (Hst[m] >= 0 ? 1u : 0u) << m;
+  return pres;
+}
+// One window row's forward update by a panel's NB columns: row j0 + dr (dr >= NB) minus
+// L(row, j0+jj) * y_jj over the columns jj < nvalid whose band reaches the row (dd = dr - jj
+// <= kl). Every load is unconditional (out-of-band entries read a valid word and use zero), so
+// the loads of all NB columns can be in flight together.
+template <typename CT, int NC>
+__device__ __forceinline__ void fwd_update(CT (&v)[NC], const CT* Lst, const CT* hv2, int dr,
+                                           int nvalid, int kl, int klp) {
+  const CT zero{};
+#pragma unroll
+  for (int jj = 0; jj < NB; ++jj) {
+    const int dd = dr - jj;                  // dd >= NB - jj >= 1 for every window row
+    const bool inb = jj < nvalid && dd <= kl;
+    const CT l0 = Lst[jj * klp + (inb ? dd - 1 : 0)];
+    const CT lv = inb ? l0 : zero;
+#pragma unroll
+    for (int c = 0; c < NC; ++c) v[c] = cfms(lv, hv2[jj * NC + c], v[c]);
+  }
+}
+// One window row's backward update: row j0 - base (base >= NB) minus U(row, j0-s2) * x_s2 for
+// the panel's columns j0-s2 with d = base - s2 <= kv, loads unconditional as above.
+template <typename CT, int NC>
+__device__ __forceinline__ void bwd_update(CT (&v)[NC], const CT* Ust, const CT* xs, int base,
+                                           int kv, int kvp) {
+  const CT zero{};
+#pragma unroll
+  for (int s2 = 0; s2 < NB; ++s2) {
+    const int d = base - s2;                 // d >= NB - s2 >= 1
+    const bool inb = d <= kv;
+    const CT u0 = Ust[(NB - 1 - s2) * kvp + (inb ? kv - d : 0)];
+    const CT uu = inb ? u0 : zero;
+#pragma unroll
+    for (int c = 0; c < NC; ++c) v[c] = cfms(uu, xs[s2 * NC + c], v[c]);
+  }
+}
+
 // One CTA's work: pole `pole`, right-hand sides grp*NC .. grp*NC+NC-1 of the solve `a`.
 template <typename CT, int NC, int SPT>
 __device__ __forceinline__ void solve_cta(const SolveArgsT<CT>& a, const int pole, const int grp) {
@@ -183,8 +225,12 @@ __device__ __forceinline__ void solve_cta(const SolveArgsT<CT>& a, const int pol
     const int* Hst = (const int*)(stage0 + (size_t)st * stage_bytes + fwd_cols_bytes + 256 * sizeof(CT));
     const int64_t j0 = P * NB;
     const int nvalid = (int)((n - j0) < NB ? (n - j0) : NB);
-    // (A) gather: head rows from hd, pivot members (H entries NB..15) from the window
-    for (int e = tid; e < NB * NC; e += T) hv[e] = hd[e];
+    // (A) gather: head rows from hd, pivot members (H entries NB..15) from the window; absent
+    // members are zero (their column of T is zero too)
+    for (int e = tid; e < NB * NC; e += T) {
+      hv[e] = hd[e];
+      if (Hst[NB + e / NC] < 0) hv[NB * NC + e] = zero;
+    }
     int mem[SPT];
 #pragma unroll
     for (int u = 0; u < SPT; ++u) {
@@ -206,16 +252,17 @@ __device__ __forceinline__ void solve_cta(const SolveArgsT<CT>& a, const int pol
     // sub-partitions, whose FP64 units are the bound), one more barrier; FP32: one thread
     // computes all partials of its output (latency, not throughput, bounds this step).
     if constexpr (sizeof(CT) == sizeof(float2)) {
+      const unsigned pres = present_mask(Hst);
       for (int e = tid; e < 16 * NC; e += T) {
         const int i = e / NC, c = e - (e / NC) * NC;
-        if (Hst[i] >= 0) {
+        if ((pres >> i) & 1u) {
           CT p[NPART];
 #pragma unroll
           for (int g = 0; g < NPART; ++g) {
             p[g] = zero;
 #pragma unroll
             for (int m = 4 * g; m < 4 * g + 4; ++m)
-              if (Hst[m] >= 0) p[g] = cfma(Tst[i * 16 + m], hv[m * NC + c], p[g]);
+              p[g] = cfma(Tst[m * 16 + i], hv[m * NC + c], p[g]);
           }
           const CT acc = sum_parts(p, 1, 0);
           hv2[e] = acc;
@@ -231,7 +278,7 @@ __device__ __forceinline__ void solve_cta(const SolveArgsT<CT>& a, const int pol
       if (Hst[i] >= 0) {
 #pragma unroll
         for (int m = 4 * g; m < 4 * g + 4; ++m)
-          if (Hst[m] >= 0) acc = cfma(Tst[i * 16 + m], hv[m * NC + c], acc);
+          if (Hst[m] >= 0) acc = cfma(Tst[m * 16 + i], hv[m * NC + c], acc);
       }
       part[e] = acc;
     }
@@ -253,20 +300,10 @@ __device__ __forceinline__ void solve_cta(const SolveArgsT<CT>& a, const int pol
       if (s >= Sf) continue;
       const int64_t r = frow[u];
       const int i = mem[u];
+      fwd_update<CT, NC>(v[u], Lst, hv2, (int)(r - j0), nvalid, kl, klp);
       if (i >= NB) {
 #pragma unroll
         for (int c = 0; c < NC; ++c) v[u][c] = hv2[i * NC + c];
-      } else {
-        const int dr = (int)(r - j0);           // 32-bit offsets inside the window
-#pragma unroll
-        for (int jj = 0; jj < NB; ++jj) {
-          const int dd = dr - jj;               // row - (j0 + jj)
-          if (jj < nvalid && dd <= kl) {        // dd >= NB - jj >= 1 for every window row
-            const CT lv = Lst[jj * klp + dd - 1];
-#pragma unroll
-            for (int c = 0; c < NC; ++c) v[u][c] = cfms(lv, hv2[jj * NC + c], v[u][c]);
-          }
-        }
       }
       // rows j0+NB..j0+2NB-1 are the next panel's head: to hd, and the slot takes row r + Sf
       const int dh = (int)(r - j0) - NB;
@@ -400,17 +437,8 @@ __device__ __forceinline__ void solve_cta(const SolveArgsT<CT>& a, const int pol
       const int s = tid + u * T;
       if (s >= Sb) continue;
       const int64_t r = row[u];
-      // d = (j0 - s2) - r in [1, kv] selects the band entries of this row
       const int base = (int)(j0 - r);            // >= NB for every window row
-#pragma unroll
-      for (int s2 = 0; s2 < NB; ++s2) {
-        const int d = base - s2;
-        if (d <= kv) {
-          const CT uu = Ust[(size_t)(NB - 1 - s2) * kvp + kv - d];
-#pragma unroll
-          for (int c = 0; c < NC; ++c) v[u][c] = cfms(uu, xs[s2 * NC + c], v[u][c]);
-        }
-      }
+      bwd_update<CT, NC>(v[u], Ust, xs, base, kv, kvp);
       // rows j0-NB..j0-2NB+1 are the next panel's head: to hd, and the slot takes row r - Sb
       const int dh = base - NB;
       if (dh < NB) {
@@ -489,8 +517,7 @@ __device__ __forceinline__ bool pwait(uint32_t bar, uint32_t parity, volatile in
   if (mbar_try_wait(bar, parity)) return true;
   const unsigned long long t0 = ie_globaltimer();
   while (true) {
-    for (int i = 0; i < 32; ++i)
-      if (mbar_try_wait(bar, parity)) return true;
+    if (mbar_try_wait_sleep(bar, parity, IE_SUSPEND_NS)) return true;
     if (*fail) return false;
     if (ie_globaltimer() - t0 > IE_WAIT_NS) {
       *fail = 1;
@@ -630,29 +657,41 @@ __global__ void __maxnreg__(REGS) band_solve_pipe_kernel(SolveArgsT<CT> a) {
       const unsigned char* st = FAC(G);
       const CT* Tst = (const CT*)(st + fwd_cols_bytes);
       const int* Hst = (const int*)(st + fwd_cols_bytes + 256 * sizeof(CT));
-      int npres = 0;
-#pragma unroll
-      for (int i = NB; i < 16; ++i) npres += Hst[i] >= 0;
+      const unsigned pres = present_mask(Hst);
+      const int npres = __popc(pres >> NB);
+      // absent members take the value zero: their column of T is zero too, so the products
+      // below can run over all 16 members unconditionally and still equal the sums over the
+      // present ones (a partial starts at +0 and so never becomes -0)
+      for (int e = lane; e < NB * NC; e += 32)
+        if (!((pres >> (NB + e / NC)) & 1u)) IN(G)[NB * NC + e] = zero;
+      __syncwarp();
       if (lane == 0 && npres < NB) mbar_arrive_cnt(HDF(G), (uint32_t)(NB - npres));
       if (!pwait(HDF(G), par(G), s_fail, a.status)) break;
       const CT* hv = IN(G);
       CT* hv2 = OUT(G);
       const int64_t j0 = P * NB;
       const int nvalid = (int)((n - j0) < NB ? (n - j0) : NB);
-      for (int e = lane; e < 16 * NC; e += 32) {
-        const int i = e / NC, c = e - (e / NC) * NC;
-        if (Hst[i] >= 0) {
+      // lanes 16h..16h+15 take the 16 outputs of one column: the reads of one T column are 16
+      // consecutive words, and no load waits behind a branch
+      constexpr int NE = (16 * NC + 31) / 32;
+#pragma unroll
+      for (int it = 0; it < NE; ++it) {
+        const int e = lane + 32 * it;
+        const int i = e & 15, c = e >> 4;
+        if (c < NC) {
           CT p[NPART];
 #pragma unroll
           for (int g = 0; g < NPART; ++g) {
             p[g] = zero;
 #pragma unroll
             for (int m = 4 * g; m < 4 * g + 4; ++m)
-              if (Hst[m] >= 0) p[g] = cfma(Tst[i * 16 + m], hv[m * NC + c], p[g]);
+              p[g] = cfma(Tst[m * 16 + i], hv[m * NC + c], p[g]);
           }
           const CT acc = sum_parts(p, 1, 0);
-          hv2[i * NC + c] = acc;
-          if (i < nvalid && c < ncol) Yo[(int64_t)(c0 + c) * a.ldy + j0 + i] = acc;
+          if ((pres >> i) & 1u) {
+            hv2[i * NC + c] = acc;
+            if (i < nvalid && c < ncol) Yo[(int64_t)(c0 + c) * a.ldy + j0 + i] = acc;
+          }
         }
       }
       __syncwarp();
@@ -715,20 +754,10 @@ __global__ void __maxnreg__(REGS) band_solve_pipe_kernel(SolveArgsT<CT> a) {
         if (s >= Sf) continue;
         const int64_t r = frow[u];
         const int i = mem[u];
+        fwd_update<CT, NC>(v[u], Lst, hv2, (int)(r - j0), nvalid, kl, klp);
         if (i >= NB) {
 #pragma unroll
           for (int c = 0; c < NC; ++c) v[u][c] = hv2[i * NC + c];
-        } else {
-          const int dr = (int)(r - j0);
-#pragma unroll
-          for (int jj = 0; jj < NB; ++jj) {
-            const int dd = dr - jj;
-            if (jj < nvalid && dd <= kl) {
-              const CT lv = Lst[jj * klp + dd - 1];
-#pragma unroll
-              for (int c = 0; c < NC; ++c) v[u][c] = cfms(lv, hv2[jj * NC + c], v[u][c]);
-            }
-          }
         }
         const int dh = (int)(r - j0) - NB;
         if (dh < NB) {   // a head row of panel P+1: hand it over, take row r + Sf
@@ -845,15 +874,7 @@ __global__ void __maxnreg__(REGS) band_solve_pipe_kernel(SolveArgsT<CT> a) {
           if (s >= Sb) continue;
           const int64_t r = row[u];
           const int base = (int)(j0 - r);
-#pragma unroll
-          for (int s2 = 0; s2 < NB; ++s2) {
-            const int d = base - s2;
-            if (d <= kv) {
-              const CT uu = Ust[(size_t)(NB - 1 - s2) * kvp + kv - d];
-#pragma unroll
-              for (int c = 0; c < NC; ++c) v[u][c] = cfms(uu, xs[s2 * NC + c], v[u][c]);
-            }
-          }
+          bwd_update<CT, NC>(v[u], Ust, xs, base, kv, kvp);
           const int dh = base - NB;
           if (dh < NB) {
             if (more) {
@@ -883,7 +904,8 @@ __global__ void __maxnreg__(REGS) band_solve_pipe_kernel(SolveArgsT<CT> a) {
 //  forward: the set H of a panel's NB steps (head rows j0..j0+NB-1, then for step jj its pivot
 //    row if it lies below the head and no earlier step named it; -1 = absent) and the 16x16
 //    matrix T such that the panel's interleaved swaps and eliminations restricted to H are
-//    H <- T H (T[:, m] = the steps applied to the unit vector of member m);
+//    H <- T H (T[:, m] = the steps applied to the unit vector of member m), stored by columns
+//    (T[i][m] at m*16 + i, so that the 16 outputs of one member read 16 consecutive words);
 //  backward: inv(U_block), the 8x8 inverse of U's diagonal block of the panel (rows and
 //    columns >= n are zero).
 // T and inv(U_block) are written in complex128 and, when T32/Ui32 are given, complex64.
@@ -944,8 +966,8 @@ __global__ void block_transform_kernel(int64_t n, int64_t n_pad, int kl, int lda
     }
     if (lane < 16) {
       const cplx t = (myrow >= 0 && present) ? val : make_double2(0, 0);
-      if (Tout) Tout[base * 256 + lane * 16 + m] = t;
-      if (T32) T32[base * 256 + lane * 16 + m] = make_float2((float)t.x, (float)t.y);
+      if (Tout) Tout[base * 256 + m * 16 + lane] = t;
+      if (T32) T32[base * 256 + m * 16 + lane] = make_float2((float)t.x, (float)t.y);
     }
   }
   // column b of inv(U_block) by back substitution: U(r, c) = A[c*ldab + kv + r - c], r <= c
