@@ -900,6 +900,476 @@ __global__ void __maxnreg__(REGS) band_solve_pipe_kernel(SolveArgsT<CT> a) {
 }
 
 // ----------------------------------------------------------------------------------------------
+// Look-ahead warp-specialised kernel. The chain that bounds the kernels above is, per panel,
+// head product -> update of the rows that form the next head -> next head product: the
+// warps holding those rows finish their whole update before the head can go on. Here the
+// update warps run one panel behind the head instead:
+//  * at panel P the update warps apply P to the window as before, and then hand the head
+//    warps the values, after panel P, of the rows panel P+2 needs (its head rows and pivot
+//    members; a member may also sit in a slot's next row, not yet in the window);
+//  * the head warps of panel P+2 apply panel P+1 to those 16 rows themselves (the same
+//    operations, in the same order, as the update warps apply to them, so the values are
+//    identical), take the rows that were members of P+1 from their own output, and form
+//    H <- T H.
+// The head warps thus never wait for an update of the current panel; the update warps have a
+// whole panel of slack. NH = NC/2 head warps take two right-hand sides each (no exchange
+// between them: every step of the head is per column). Stage G of the ring holds the factor
+// panel (forward: L columns, T, H(G) and H(G+2), the member set two panels on; backward: U
+// columns, inv(U_block)), OUT(G) (forward: T H; backward: x_head) and IN(G) (the rows the head
+// of G needs, after panel G-2). Per stage four mbarriers:
+//   FULL  (bulk copy landed; count 1 + tx bytes),
+//   EMPTY (every update warp is done with the stage, and every head warp with it and with the
+//          catch-up of the next panel; count WU + NH),
+//   HDF   (IN complete; count 2*NB: one arrival per delivered row, the rest by head warp 0),
+//   XSF   (OUT complete; count NH).
+// Panels 0 and 1 of each sweep read their inputs directly (no panel before them has touched
+// them). The update warps write IN(G+2) while processing G; stage G+2's previous use
+// (G+2-ns) ended with head G+3-ns, before head G, for ns >= 4. Every wait is bounded.
+template <typename CT, int NC, int SPT, int REGS>
+__global__ void __maxnreg__(REGS) band_solve_la_kernel(SolveArgsT<CT> a) {
+  constexpr int HC = NC >= 2 ? 2 : 1;          // right-hand sides per head warp
+  constexpr int NH = NC / HC;                  // head warps
+  const int pole = blockIdx.y;
+  const int c0 = blockIdx.x * NC;
+  const int ncol = min(NC, a.k - c0);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int WU = (int)(blockDim.x >> 5) - NH - 1;   // update warps
+  const int TU = WU * 32;
+  const int kl = a.kl, kv = a.kv, klp = a.klp, kvp = a.kvp;
+  const int64_t n = a.n;
+  const CT* Lp = a.L + (int64_t)pole * a.lstride;
+  const CT* Up = a.U + (int64_t)pole * a.ustride;
+  const int64_t npan = a.n_pad / NB;
+  const CT* Tp = a.Tb + (int64_t)pole * npan * 256;
+  const int* Hp = a.Hb + (int64_t)pole * npan * 16;
+  const CT* Uip = a.Ub + (int64_t)pole * npan * 64;
+  const CT* R = a.RHS + (int64_t)pole * a.rstride;
+  CT* Yo = a.Y + (int64_t)pole * a.ystride;
+  cplx* Xo = a.X + (int64_t)pole * a.xstride;
+  const cplx w = a.weights[pole];
+  const CT zero{};
+  const int ns = a.nstage;
+  const int64_t npanel = npan, total = 2 * npan;
+
+  extern __shared__ __align__(128) unsigned char sm_raw[];
+  uint64_t* bars = (uint64_t*)sm_raw;             // [4][ns]: FULL, EMPTY, HDF, XSF
+  const size_t fwd_cols_bytes = (size_t)NB * klp * sizeof(CT);
+  const size_t bwd_cols_bytes = (size_t)NB * kvp * sizeof(CT);
+  const size_t fwd_bytes = fwd_cols_bytes + 256 * sizeof(CT) + 32 * sizeof(int);
+  const size_t bwd_bytes = bwd_cols_bytes + 64 * sizeof(CT);
+  const size_t fac_bytes = ((fwd_bytes > bwd_bytes ? fwd_bytes : bwd_bytes) + 127) & ~(size_t)127;
+  const size_t io_bytes = (size_t)16 * NC * sizeof(CT);
+  const size_t stage_bytes = (fac_bytes + 2 * io_bytes + 127) & ~(size_t)127;
+  unsigned char* stage0 = sm_raw + ((4 * (size_t)ns * 8 + 127) & ~(size_t)127);
+  __shared__ int s_fail_raw;
+  volatile int* s_fail = &s_fail_raw;
+  {
+    unsigned dsz;
+    asm("mov.u32 %0, %%dynamic_smem_size;" : "=r"(dsz));
+    if ((size_t)(stage0 - sm_raw) + (size_t)ns * stage_bytes > (size_t)dsz || WU < 1 || ns < 4) {
+      if (tid == 0) atomicExch(a.status + ST_TIMEOUT, 1);
+      return;
+    }
+  }
+  auto FULL = [&](int s) { return smem_u32(&bars[0 * ns + s]); };
+  auto EMPTY = [&](int s) { return smem_u32(&bars[1 * ns + s]); };
+  auto HDF = [&](int s) { return smem_u32(&bars[2 * ns + s]); };
+  auto XSF = [&](int s) { return smem_u32(&bars[3 * ns + s]); };
+  auto FAC = [&](int s) { return stage0 + (size_t)s * stage_bytes; };
+  auto OUT = [&](int s) { return (CT*)(stage0 + (size_t)s * stage_bytes + fac_bytes); };
+  auto IN = [&](int s) { return (CT*)(stage0 + (size_t)s * stage_bytes + fac_bytes + io_bytes); };
+  auto HS = [&](int s) { return (const int*)(FAC(s) + fwd_cols_bytes + 256 * sizeof(CT)); };
+  auto HS2 = [&](int s) { return HS(s) + 16; };
+  // ring position of a panel as running counters: stage s (G mod ns) and parity ph
+  auto advance = [&](int& s, uint32_t& ph) {
+    if (++s == ns) { s = 0; ph ^= 1u; }
+  };
+  auto plus = [&](int s, int d) { return s + d >= ns ? s + d - ns : s + d; };   // 0 <= d < ns
+  auto minus1 = [&](int s) { return s == 0 ? ns - 1 : s - 1; };
+  if (tid == 0) {
+    s_fail_raw = 0;
+    for (int i = 0; i < ns; ++i) {
+      mbar_init(FULL(i), 1);
+      mbar_init(EMPTY(i), (uint32_t)(WU + NH));
+      mbar_init(HDF(i), 2 * NB);
+      mbar_init(XSF(i), (uint32_t)NH);
+    }
+    mbar_fence_init();
+  }
+  __syncthreads();
+
+  const int Sf = kl > 2 * NB ? kl : 2 * NB;    // forward window (two heads ahead must fit)
+  const int Sb = kv > 2 * NB ? kv : 2 * NB;
+  const bool is_prod = warp == WU + NH, is_head = warp >= WU && warp < WU + NH;
+  const int hw = warp - WU;                    // head warp index
+  // ---------------------------------------------------------------- producer warp
+  int p_s = 0;
+  uint32_t p_ph = 0;
+  int64_t issued = 0;
+  auto issue = [&](int64_t G, int s) {
+    unsigned char* dst = FAC(s);
+    const uint32_t bar = FULL(s);
+    if (G < npanel) {
+      const int64_t P = G;
+      const bool h2 = P + 2 < npanel;
+      mbar_expect_tx(bar, (uint32_t)(fwd_cols_bytes + 256 * sizeof(CT) + (h2 ? 32 : 16) * sizeof(int)));
+      bulk_g2s(smem_u32(dst), Lp + P * NB * a.ldl, (uint32_t)fwd_cols_bytes, bar);
+      bulk_g2s(smem_u32(dst + fwd_cols_bytes), Tp + P * 256, (uint32_t)(256 * sizeof(CT)), bar);
+      bulk_g2s(smem_u32(dst + fwd_cols_bytes + 256 * sizeof(CT)), Hp + P * 16,
+               (uint32_t)(16 * sizeof(int)), bar);
+      if (h2)
+        bulk_g2s(smem_u32(dst + fwd_cols_bytes + 256 * sizeof(CT) + 16 * sizeof(int)),
+                 Hp + (P + 2) * 16, (uint32_t)(16 * sizeof(int)), bar);
+    } else {
+      const int64_t cb0 = a.n_pad - (G - npanel + 1) * NB;
+      mbar_expect_tx(bar, (uint32_t)bwd_bytes);
+      bulk_g2s(smem_u32(dst), Up + cb0 * a.ldu, (uint32_t)bwd_cols_bytes, bar);
+      bulk_g2s(smem_u32(dst + bwd_cols_bytes), Uip + (cb0 / NB) * 64, (uint32_t)(64 * sizeof(CT)),
+               bar);
+    }
+  };
+  auto produce_until = [&](int64_t Gend) {   // lane 0 of the producer warp
+    for (; issued < Gend && !*s_fail; ++issued, advance(p_s, p_ph)) {
+      if (issued >= ns && !pwait(EMPTY(p_s), p_ph ^ 1u, s_fail, a.status)) break;
+      issue(issued, p_s);
+    }
+  };
+  auto drain = [&]() {   // wait for the bulk copies still in flight (bounded)
+    int s = p_s;
+    uint32_t ph = p_ph;
+    for (int64_t G = issued - 1; G >= 0 && G >= issued - ns; --G) {
+      if (s == 0) { s = ns - 1; ph ^= 1u; } else { --s; }
+      if (!mbar_wait_bounded(FULL(s), ph)) atomicExch(a.status + ST_TIMEOUT, 1);
+    }
+  };
+
+  CT v[SPT][NC], nxt[SPT][NC];
+  int64_t frow[SPT];
+  // the update warps' ring position (both sweeps)
+  int u_s = 0;
+  uint32_t u_ph = 0;
+  // the head warps' ring position
+  int h_s = 0;
+  uint32_t h_ph = 0;
+  // ---------------------------------------------------------------- forward sweep
+  if (is_prod) {
+    if (lane == 0) produce_until(npanel + ns < total ? npanel + ns : total);
+  } else if (is_head) {
+    // lane -> (member i, right-hand side c): 16 lanes per column, HC columns per warp
+    const int i = lane & 15, cc = lane >> 4, c = hw * HC + cc;
+    const bool act = cc < HC;
+    for (int64_t P = 0; P < npanel; ++P, advance(h_s, h_ph)) {
+      const int s = h_s;
+      if (!pwait(FULL(s), h_ph, s_fail, a.status)) break;
+      const int* H = HS(s);
+      const unsigned pres = present_mask(H);
+      CT* in = IN(s);
+      if (P < 2) {
+        // no panel has touched these rows yet: read them from the right-hand side
+        if (act) {
+          const int r = H[i];
+          in[i * NC + c] = (r >= 0 && r < n && c < ncol) ? R[(int64_t)(c0 + c) * a.ldr + r] : zero;
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive_cnt(HDF(s), hw == 0 ? (uint32_t)(2 * NB - (NH - 1)) : 1u);
+      } else if (hw == 0 && lane == 0) {
+        const int npres = __popc(pres >> NB);
+        if (npres < NB) mbar_arrive_cnt(HDF(s), (uint32_t)(NB - npres));
+      }
+      if (!pwait(HDF(s), h_ph, s_fail, a.status)) break;
+      const int64_t j0 = P * NB;
+      const int nvalid = (int)((n - j0) < NB ? (n - j0) : NB);
+      // catch-up: the members after panel P-1 (IN holds them after panel P-2); members of
+      // panel P-1 take its output, the others apply its NB columns as the update warps do
+      if (act) {
+        const int r = H[i];
+        CT val = zero;
+        if (r >= 0) {
+          val = in[i * NC + c];
+          if (P >= 1) {
+            const int sp = minus1(s);
+            const int* Hq = HS(sp);
+            const CT* oq = OUT(sp);
+            int idx = -1;
+#pragma unroll
+            for (int m = NB; m < 16; ++m)
+              if (Hq[m] == r) idx = m;
+            if (idx >= 0) {
+              val = oq[idx * NC + c];
+            } else {
+              const CT* Lq = (const CT*)FAC(sp);
+              const int64_t jq = j0 - NB;
+              const int nvq = (int)((n - jq) < NB ? (n - jq) : NB);
+              const int dr = (int)(r - jq);
+#pragma unroll
+              for (int jj = 0; jj < NB; ++jj) {
+                const int dd = dr - jj;
+                const bool inb = jj < nvq && dd <= kl;
+                const CT l0 = Lq[jj * klp + (inb ? dd - 1 : 0)];
+                val = cfms(inb ? l0 : zero, oq[jj * NC + c], val);
+              }
+            }
+          }
+        }
+        in[i * NC + c] = val;
+      }
+      __syncwarp();
+      // H <- T H
+      if (act) {
+        const CT* Tst = (const CT*)(FAC(s) + fwd_cols_bytes);
+        CT p[NPART];
+#pragma unroll
+        for (int g = 0; g < NPART; ++g) {
+          p[g] = zero;
+#pragma unroll
+          for (int m = 4 * g; m < 4 * g + 4; ++m) p[g] = cfma(Tst[m * 16 + i], in[m * NC + c], p[g]);
+        }
+        const CT acc = sum_parts(p, 1, 0);
+        if ((pres >> i) & 1u) {
+          OUT(s)[i * NC + c] = acc;
+          if (i < nvalid && c < ncol) Yo[(int64_t)(c0 + c) * a.ldy + j0 + i] = acc;
+        }
+      }
+      __syncwarp();
+      if (lane == 0) {
+        mbar_arrive(XSF(s));
+        if (P >= 1) mbar_arrive(EMPTY(minus1(s)));   // panel P-1's factors and output
+      }
+    }
+    if (!*s_fail && lane == 0 && npanel > 0) mbar_arrive(EMPTY(minus1(h_s)));
+  } else {
+    // update warps: window rows NB + slot, next rows NB + slot + Sf
+#pragma unroll
+    for (int u = 0; u < SPT; ++u) {
+      const int sl = tid + u * TU;
+      const int64_t r = NB + sl;
+      frow[u] = r;
+#pragma unroll
+      for (int c = 0; c < NC; ++c) {
+        v[u][c] = (sl < Sf && r < n && c < ncol) ? R[(int64_t)(c0 + c) * a.ldr + r] : zero;
+        nxt[u][c] = (sl < Sf && r + Sf < n && c < ncol) ? R[(int64_t)(c0 + c) * a.ldr + r + Sf] : zero;
+      }
+    }
+    for (int64_t P = 0; P < npanel; ++P, advance(u_s, u_ph)) {
+      const int s = u_s;
+      if (!pwait(FULL(s), u_ph, s_fail, a.status)) break;
+      if (!pwait(XSF(s), u_ph, s_fail, a.status)) break;
+      const CT* Lst = (const CT*)FAC(s);
+      const int* H = HS(s);
+      const int* H2 = HS2(s);
+      const CT* hv2 = OUT(s);
+      const int64_t j0 = P * NB;
+      const int nvalid = (int)((n - j0) < NB ? (n - j0) : NB);
+      const bool deliver = P + 2 < npanel;
+      const int s2 = plus(s, 2);
+      CT* in2 = IN(s2);
+      int hm[NB], h2m[NB];
+#pragma unroll
+      for (int m = 0; m < NB; ++m) {
+        hm[m] = H[NB + m];
+        h2m[m] = deliver ? H2[NB + m] : -1;
+      }
+#pragma unroll
+      for (int u = 0; u < SPT; ++u) {
+        const int sl = tid + u * TU;
+        if (sl >= Sf) continue;
+        const int64_t r = frow[u];
+        const int ri = (int)r;
+        const int dr = (int)(r - j0);
+        fwd_update<CT, NC>(v[u], Lst, hv2, dr, nvalid, kl, klp);
+        int mem = -1;
+#pragma unroll
+        for (int m = 0; m < NB; ++m)
+          if (hm[m] == ri) mem = NB + m;
+        if (mem >= 0) {
+#pragma unroll
+          for (int c = 0; c < NC; ++c) v[u][c] = hv2[mem * NC + c];
+        }
+        if (deliver) {
+          // rows of panel P+2's set: its head rows, members in this row or in the next row
+          const int d2 = dr - 2 * NB;
+          if (d2 >= 0 && d2 < NB) {
+#pragma unroll
+            for (int c = 0; c < NC; ++c) in2[d2 * NC + c] = v[u][c];
+            mbar_arrive(HDF(s2));
+          }
+          int mv = -1, mn = -1;
+#pragma unroll
+          for (int m = 0; m < NB; ++m) {
+            if (h2m[m] == ri) mv = NB + m;
+            if (h2m[m] == ri + Sf) mn = NB + m;
+          }
+          if (mv >= 0) {
+#pragma unroll
+            for (int c = 0; c < NC; ++c) in2[mv * NC + c] = v[u][c];
+            mbar_arrive(HDF(s2));
+          }
+          if (mn >= 0) {
+#pragma unroll
+            for (int c = 0; c < NC; ++c) in2[mn * NC + c] = nxt[u][c];
+            mbar_arrive(HDF(s2));
+          }
+        }
+        if (dr - NB < NB) {   // a head row of panel P+1 (the head warps finish it): take r + Sf
+          const int64_t r2 = r + Sf;
+          frow[u] = r2;
+#pragma unroll
+          for (int c = 0; c < NC; ++c) {
+            v[u][c] = nxt[u][c];
+            nxt[u][c] = (r2 + Sf < n && c < ncol) ? R[(int64_t)(c0 + c) * a.ldr + r2 + Sf] : zero;
+          }
+        }
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(EMPTY(s));
+    }
+  }
+  // the forward results y (written by the head warps) are read back by every warp below
+  __syncthreads();
+
+  // ---------------------------------------------------------------- backward sweep
+  if (*s_fail) {
+    if (is_prod && lane == 0) drain();
+    return;
+  }
+  if (is_prod) {
+    if (lane == 0) {
+      produce_until(total);
+      // stay until every stage has been consumed, so that no bulk copy can outlive the CTA
+      int s = p_s;
+      uint32_t ph = p_ph;
+      for (int64_t G = total - 1; G >= 0 && G >= total - ns && !*s_fail; --G) {
+        if (s == 0) { s = ns - 1; ph ^= 1u; } else { --s; }
+        pwait(EMPTY(s), ph, s_fail, a.status);
+      }
+      if (*s_fail) drain();
+    }
+  } else if (is_head) {
+    // lane -> (head row t, right-hand side c): 8 lanes per column
+    const int t = lane & 7, cc = lane >> 3, c = hw * HC + cc;
+    const bool act = cc < HC;
+    for (int64_t Bp = 0; Bp < npanel; ++Bp, advance(h_s, h_ph)) {
+      const int s = h_s;
+      if (!pwait(FULL(s), h_ph, s_fail, a.status)) break;
+      const int64_t j0 = a.n_pad - 1 - Bp * NB;
+      CT* in = IN(s);
+      if (Bp < 2) {
+        if (act) {
+          const int64_t r = j0 - t;
+          in[t * NC + c] = (r < n && c < ncol) ? Yo[(int64_t)(c0 + c) * a.ldy + r] : zero;
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive_cnt(HDF(s), hw == 0 ? (uint32_t)(2 * NB - (NH - 1)) : 1u);
+      } else if (hw == 0 && lane == 0) {
+        mbar_arrive_cnt(HDF(s), NB);
+      }
+      if (!pwait(HDF(s), h_ph, s_fail, a.status)) break;
+      // catch-up: the head rows after panel Bp-1, from their values after panel Bp-2
+      if (act) {
+        CT val = in[t * NC + c];
+        if (Bp >= 1) {
+          const int sp = minus1(s);
+          const CT* Uq = (const CT*)FAC(sp);
+          const CT* xq = OUT(sp);
+          const int base = NB + t;
+#pragma unroll
+          for (int s2 = 0; s2 < NB; ++s2) {
+            const int d = base - s2;
+            const bool inb = d <= kv;
+            const CT u0 = Uq[(NB - 1 - s2) * kvp + (inb ? kv - d : 0)];
+            val = cfms(inb ? u0 : zero, xq[s2 * NC + c], val);
+          }
+        }
+        in[t * NC + c] = val;
+      }
+      __syncwarp();
+      if (act) {
+        const CT* Uist = (const CT*)(FAC(s) + bwd_cols_bytes);
+        CT p[NPART];
+#pragma unroll
+        for (int g = 0; g < NPART; ++g) {
+          p[g] = zero;
+#pragma unroll
+          for (int t2 = 2 * g; t2 < 2 * g + 2; ++t2)
+            p[g] = cfma(Uist[(NB - 1 - t) * NB + (NB - 1 - t2)], in[t2 * NC + c], p[g]);
+        }
+        const CT acc = sum_parts(p, 1, 0);
+        OUT(s)[t * NC + c] = acc;
+        const int64_t r = j0 - t;
+        if (r < n && c < ncol) {
+          if constexpr (sizeof(CT) == sizeof(cplx)) {
+            if (a.mode == 0) Yo[(int64_t)(c0 + c) * a.ldy + r] = cmul(w, acc);
+          }
+          if (a.mode == 1) Xo[(int64_t)(c0 + c) * a.ldx + r] = to_d(acc);
+          else if (a.mode == 3) Yo[(int64_t)(c0 + c) * a.ldy + r] = acc;
+        }
+      }
+      __syncwarp();
+      if (lane == 0) {
+        mbar_arrive(XSF(s));
+        if (Bp >= 1) mbar_arrive(EMPTY(minus1(s)));
+      }
+    }
+    if (!*s_fail && lane == 0 && npanel > 0) mbar_arrive(EMPTY(minus1(h_s)));
+  } else {
+    int64_t row[SPT];
+    {
+      const int64_t j0 = a.n_pad - 1;
+#pragma unroll
+      for (int u = 0; u < SPT; ++u) {
+        const int sl = tid + u * TU;
+        const int64_t r = j0 - NB - sl;
+        row[u] = r;
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+          v[u][c] = (sl < Sb && r >= 0 && r < n && c < ncol) ? Yo[(int64_t)(c0 + c) * a.ldy + r] : zero;
+          const int64_t rn = r - Sb;
+          nxt[u][c] = (sl < Sb && rn >= 0 && rn < n && c < ncol) ? Yo[(int64_t)(c0 + c) * a.ldy + rn]
+                                                                : zero;
+        }
+      }
+    }
+    for (int64_t Bp = 0; Bp < npanel; ++Bp, advance(u_s, u_ph)) {
+      const int s = u_s;
+      if (!pwait(FULL(s), u_ph, s_fail, a.status)) break;
+      if (!pwait(XSF(s), u_ph, s_fail, a.status)) break;
+      const CT* Ust = (const CT*)FAC(s);
+      const CT* xs = OUT(s);
+      const int64_t j0 = a.n_pad - 1 - Bp * NB;
+      const bool deliver = Bp + 2 < npanel;
+      const int s2 = plus(s, 2);
+      CT* in2 = IN(s2);
+#pragma unroll
+      for (int u = 0; u < SPT; ++u) {
+        const int sl = tid + u * TU;
+        if (sl >= Sb) continue;
+        const int64_t r = row[u];
+        const int base = (int)(j0 - r);
+        bwd_update<CT, NC>(v[u], Ust, xs, base, kv, kvp);
+        const int t2 = base - 2 * NB;   // a head row of panel Bp+2
+        if (deliver && t2 >= 0 && t2 < NB) {
+#pragma unroll
+          for (int c = 0; c < NC; ++c) in2[t2 * NC + c] = v[u][c];
+          mbar_arrive(HDF(s2));
+        }
+        if (base - NB < NB) {   // a head row of panel Bp+1: take row r - Sb
+          const int64_t r2 = r - Sb;
+          row[u] = r2;
+#pragma unroll
+          for (int c = 0; c < NC; ++c) {
+            v[u][c] = nxt[u][c];
+            const int64_t rn = r2 - Sb;
+            nxt[u][c] = (rn >= 0 && rn < n && c < ncol) ? Yo[(int64_t)(c0 + c) * a.ldy + rn] : zero;
+          }
+        }
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(EMPTY(s));
+    }
+  }
+}
+
+// ----------------------------------------------------------------------------------------------
 // Block transforms, computed once per factorisation (one warp per (panel, pole)):
 //  forward: the set H of a panel's NB steps (head rows j0..j0+NB-1, then for step jj its pivot
 //    row if it lies below the head and no earlier step named it; -1 = absent) and the 16x16
@@ -1052,8 +1522,33 @@ static cudaError_t launch_pipe_t(const SolveArgsT<CT>& a, int q, int threads, si
   return cudaErrorInvalidValue;
 }
 
+template <typename CT, int NC, int SPT, int REGS>
+static cudaError_t launch_la_r(const SolveArgsT<CT>& a, int q, int threads, size_t smem,
+                               cudaStream_t s) {
+  auto kfn = band_solve_la_kernel<CT, NC, SPT, REGS>;
+  cudaError_t e = ie_smem_optin((const void*)kfn);
+  if (e != cudaSuccess) return e;
+  int blocks = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, kfn, threads, smem);
+  if (e != cudaSuccess) return e;
+  if (blocks < 1) return cudaErrorLaunchOutOfResources;
+  dim3 grid((unsigned)((a.k + NC - 1) / NC), (unsigned)q);
+  kfn<<<grid, threads, smem, s>>>(a); ie_count_launch();
+  return cudaGetLastError();
+}
+
+template <typename CT, int NC, int SPT>
+static cudaError_t launch_la_t(const SolveArgsT<CT>& a, int q, int threads, size_t smem,
+                               cudaStream_t s) {
+  const int wps = (threads / 32 + 3) / 4;
+  if (wps <= 3) return launch_la_r<CT, NC, SPT, 168>(a, q, threads, smem, s);
+  if (wps <= 4) return launch_la_r<CT, NC, SPT, 128>(a, q, threads, smem, s);
+  if (wps <= 5) return launch_la_r<CT, NC, SPT, 96>(a, q, threads, smem, s);
+  return cudaErrorInvalidValue;
+}
+
 // One launch shape: NC right-hand sides per CTA, SPT window slots per thread, at most
-// `stages` staged panels; pipe = 1 for the warp-specialised kernel.
+// `stages` staged panels; pipe = 1 for the warp-specialised kernel, 2 for its look-ahead form.
 struct SolveCfg {
   int nc, spt, stages, pipe;
 };
@@ -1062,6 +1557,27 @@ struct SolveCfg {
 template <typename CT>
 static bool shape_for(SolveArgsT<CT>& a, const SolveCfg& c, int* threads, size_t* smem) {
   const int slots = a.kv > NB ? a.kv : NB;     // backward window (at least the forward's)
+  if (c.pipe == 2) {
+    // update warps for the window (at least two heads deep), the head warps (two right-hand
+    // sides each) and the producer warp
+    const int slots2 = a.kv > 2 * NB ? a.kv : 2 * NB;
+    const int nh = c.nc >= 2 ? c.nc / 2 : 1;
+    const int wu = ((slots2 + c.spt - 1) / c.spt + 31) / 32;
+    *threads = (wu + nh + 1) * 32;
+    if (*threads > 640) return false;
+    const size_t fwdb = (size_t)NB * a.klp * sizeof(CT) + 256 * sizeof(CT) + 32 * sizeof(int);
+    const size_t bwdb = (size_t)NB * a.kvp * sizeof(CT) + 64 * sizeof(CT);
+    const size_t fac = ((fwdb > bwdb ? fwdb : bwdb) + 127) & ~(size_t)127;
+    const size_t stage_bytes = (fac + 2 * (size_t)16 * c.nc * sizeof(CT) + 127) & ~(size_t)127;
+    const size_t budget = 210 * 1024;
+    int nstage = c.stages > 4 ? c.stages : 4;
+    auto need = [&](int k) { return ((4 * (size_t)k * 8 + 127) & ~(size_t)127) + k * stage_bytes; };
+    while (nstage > 4 && need(nstage) > budget) --nstage;
+    if (need(nstage) > budget) return false;
+    a.nstage = nstage;
+    *smem = need(nstage);
+    return true;
+  }
   if (c.pipe) {
     // update warps for the window, then the head warp and the producer warp
     const int wu = ((slots + c.spt - 1) / c.spt + 31) / 32;
@@ -1105,8 +1621,9 @@ static cudaError_t launch_cfg(SolveArgsT<CT> a, int q, const SolveCfg& c, cudaSt
   if (!shape_for(a, c, &threads, &smem)) return cudaErrorInvalidValue;
 #define IE_SOLVE_CASE(NC_, SPT_)                                                             \
   if (c.nc == NC_ && c.spt == SPT_)                                                          \
-    return c.pipe ? launch_pipe_t<CT, NC_, SPT_>(a, q, threads, smem, s)                     \
-                  : launch_solve_t<CT, NC_, SPT_>(a, q, threads, smem, s);
+    return c.pipe == 2 ? launch_la_t<CT, NC_, SPT_>(a, q, threads, smem, s)                  \
+           : c.pipe    ? launch_pipe_t<CT, NC_, SPT_>(a, q, threads, smem, s)                \
+                       : launch_solve_t<CT, NC_, SPT_>(a, q, threads, smem, s);
   IE_SOLVE_CASE(1, 1) IE_SOLVE_CASE(2, 1) IE_SOLVE_CASE(4, 1)
   IE_SOLVE_CASE(1, 2) IE_SOLVE_CASE(2, 2) IE_SOLVE_CASE(4, 2)
   if constexpr (sizeof(CT) == sizeof(float2)) {
@@ -1194,6 +1711,15 @@ static cudaError_t launch_tuned(const SolveArgsT<CT>& a, int q, cudaStream_t s) 
         c.push_back({8, spt0, 4, 1});
         c.push_back({8, 2, 3, 1});
       }
+      // its look-ahead form
+      c.push_back({4, spt0, 6, 2});
+      c.push_back({4, 2, 6, 2});
+      c.push_back({2, spt0, 6, 2});
+      c.push_back({2, 2, 6, 2});
+      if (fp32) {
+        c.push_back({8, spt0, 6, 2});
+        c.push_back({8, 2, 6, 2});
+      }
       for (const SolveCfg& x : c) {
         if (x.spt < spt0) continue;
         bool dup = false;
@@ -1228,7 +1754,8 @@ static cudaError_t launch_tuned(const SolveArgsT<CT>& a, int q, cudaStream_t s) 
           fprintf(stderr, "band solve tuner (elem %d B, kl %d, q %d, k <= %d):", key.esize, key.kl,
                   key.q, key.kb);
           for (size_t i = 0; i < T.cand.size(); ++i)
-            fprintf(stderr, " [%s nc %d spt %d stages %d: %.3f ms]", T.cand[i].pipe ? "pipe" : "sync",
+            fprintf(stderr, " [%s nc %d spt %d stages %d: %.3f ms]",
+                    T.cand[i].pipe == 2 ? "look-ahead" : T.cand[i].pipe ? "pipe" : "sync",
                     T.cand[i].nc, T.cand[i].spt, T.cand[i].stages, T.ms[i]);
           fprintf(stderr, " -> %d\n", b);
         }

@@ -385,8 +385,8 @@ def test_simple_rule_handle_equals_composite(ie, c1):
 @pytest.mark.parametrize("name", ["c1_m24", "r1_m37"])
 def test_every_solve_shape_gives_identical_results(ie, name):
     """The band-solve tuner times each candidate launch shape once (columns per CTA, window
-    slots per thread, staged panels, and the barrier-synchronised or warp-specialised kernel)
-    on real calls. Every shape performs the same floating-point operations in the same order
+    slots per thread, staged panels, and the barrier-synchronised, warp-specialised or
+    look-ahead kernel) on real calls. Every shape performs the same floating-point operations in the same order
     per column, so repeated ie_apply_G calls, which walk through all shapes, must return
     bit-identical blocks; the first one also matches the oracle."""
     c = Case(ie, name)
@@ -395,7 +395,7 @@ def test_every_solve_shape_gives_identical_results(ie, name):
         V = ie_inputs.random_block(c.n, k, seed=12)
         Vd = dblock(V)
         outs = []
-        for _ in range(18):                       # more calls than candidate shapes
+        for _ in range(24):                       # more calls than candidate shapes
             GVd = dzeros(c.n, k)
             assert ie.ie_apply_G(c.h, Vd, GVd) == ie.IE_OK
             outs.append(GVd.cpu().numpy())
