@@ -53,9 +53,10 @@ __device__ __forceinline__ bool mbar_try_wait_sleep(uint32_t bar, uint32_t parit
   return ok != 0;
 }
 constexpr uint32_t IE_SUSPEND_NS = 20000;   // one suspended try_wait lasts at most ~20 us
-// bounded wait: false after IE_WAIT_NS
+// bounded wait: false after IE_WAIT_NS (the clock is read only once the first suspended wait
+// has run out)
 __device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity) {
-  if (mbar_try_wait(bar, parity)) return true;
+  if (mbar_try_wait_sleep(bar, parity, IE_SUSPEND_NS)) return true;
   const unsigned long long t0 = ie_globaltimer();
   while (true) {
     if (mbar_try_wait_sleep(bar, parity, IE_SUSPEND_NS)) return true;

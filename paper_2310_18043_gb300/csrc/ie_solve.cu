@@ -75,10 +75,31 @@ struct SolveArgsT {
 // 512), so every sub-partition of the SM gets the same share of the update.
 // Bit m set: member m of the panel's set H is present (H entry >= 0).
 __device__ __forceinline__ unsigned present_mask(const int* Hst) {
+  const int4* h4 = reinterpret_cast<const int4*>(Hst);   // 16-byte aligned in every stage
   unsigned pres = 0;
 #pragma unroll
-  for (int m = 0; m < 16; ++m) pres |= (Hst[m] >= 0 ? 1u : 0u) << m;
+  for (int k = 0; k < 4; ++k) {
+    const int4 t = h4[k];
+    pres |= ((t.x >= 0 ? 1u : 0u) | (t.y >= 0 ? 2u : 0u) | (t.z >= 0 ? 4u : 0u) |
+             (t.w >= 0 ? 8u : 0u)) << (4 * k);
+  }
   return pres;
+}
+// the NC values of one head output row (NC even, complex64: 16-byte loads)
+template <typename CT, int NC>
+__device__ __forceinline__ void ld_row(const CT* p, CT (&o)[NC]) {
+  if constexpr (sizeof(CT) == sizeof(float2) && NC % 2 == 0) {
+    const float4* q = reinterpret_cast<const float4*>(p);
+#pragma unroll
+    for (int k = 0; k < NC / 2; ++k) {
+      const float4 t = q[k];
+      o[2 * k] = make_float2(t.x, t.y);
+      o[2 * k + 1] = make_float2(t.z, t.w);
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < NC; ++k) o[k] = p[k];
+  }
 }
 // One window row's forward update by a panel's NB columns: row j0 + dr (dr >= NB) minus
 // L(row, j0+jj) * y_jj over the columns jj < nvalid whose band reaches the row (dd = dr - jj
@@ -94,8 +115,10 @@ __device__ __forceinline__ void fwd_update(CT (&v)[NC], const CT* Lst, const CT*
     const bool inb = jj < nvalid && dd <= kl;
     const CT l0 = Lst[jj * klp + (inb ? dd - 1 : 0)];
     const CT lv = inb ? l0 : zero;
+    CT x[NC];
+    ld_row<CT, NC>(hv2 + jj * NC, x);
 #pragma unroll
-    for (int c = 0; c < NC; ++c) v[c] = cfms(lv, hv2[jj * NC + c], v[c]);
+    for (int c = 0; c < NC; ++c) v[c] = cfms(lv, x[c], v[c]);
   }
 }
 // One window row's backward update: row j0 - base (base >= NB) minus U(row, j0-s2) * x_s2 for
@@ -110,8 +133,10 @@ __device__ __forceinline__ void bwd_update(CT (&v)[NC], const CT* Ust, const CT*
     const bool inb = d <= kv;
     const CT u0 = Ust[(NB - 1 - s2) * kvp + (inb ? kv - d : 0)];
     const CT uu = inb ? u0 : zero;
+    CT x[NC];
+    ld_row<CT, NC>(xs + s2 * NC, x);
 #pragma unroll
-    for (int c = 0; c < NC; ++c) v[c] = cfms(uu, xs[s2 * NC + c], v[c]);
+    for (int c = 0; c < NC; ++c) v[c] = cfms(uu, x[c], v[c]);
   }
 }
 
@@ -514,7 +539,7 @@ __device__ __forceinline__ void mbar_arrive_cnt(uint32_t bar, uint32_t cnt) {
 // recorded in the CTA's flag and in the kernel's status word
 __device__ __forceinline__ bool pwait(uint32_t bar, uint32_t parity, volatile int* fail,
                                       int* status) {
-  if (mbar_try_wait(bar, parity)) return true;
+  if (mbar_try_wait_sleep(bar, parity, IE_SUSPEND_NS)) return true;
   const unsigned long long t0 = ie_globaltimer();
   while (true) {
     if (mbar_try_wait_sleep(bar, parity, IE_SUSPEND_NS)) return true;
