@@ -948,8 +948,10 @@ __global__ void __maxnreg__(REGS) band_solve_pipe_kernel(SolveArgsT<CT> a) {
 //   HDF   (IN complete; count 2*NB: one arrival per delivered row, the rest by head warp 0),
 //   XSF   (OUT complete; count NH).
 // Panels 0 and 1 of each sweep read their inputs directly (no panel before them has touched
-// them). The update warps write IN(G+2) while processing G; stage G+2's previous use
-// (G+2-ns) ended with head G+3-ns, before head G, for ns >= 4. Every wait is bounded.
+// them). The update warps write IN(G+2) while processing G (after head G): the stage's
+// previous use G+2-ns was last read by head G+2-ns (IN) and head G+3-ns (factors and OUT of
+// the catch-up), both before head G for ns >= 3, and the update warps still reading OUT(G-1)
+// for ns = 3 touch another part of the stage. Every wait is bounded.
 template <typename CT, int NC, int SPT, int REGS>
 __global__ void __maxnreg__(REGS) band_solve_la_kernel(SolveArgsT<CT> a) {
   constexpr int HC = NC >= 2 ? 2 : 1;          // right-hand sides per head warp
@@ -991,7 +993,7 @@ __global__ void __maxnreg__(REGS) band_solve_la_kernel(SolveArgsT<CT> a) {
   {
     unsigned dsz;
     asm("mov.u32 %0, %%dynamic_smem_size;" : "=r"(dsz));
-    if ((size_t)(stage0 - sm_raw) + (size_t)ns * stage_bytes > (size_t)dsz || WU < 1 || ns < 4) {
+    if ((size_t)(stage0 - sm_raw) + (size_t)ns * stage_bytes > (size_t)dsz || WU < 1 || ns < 3) {
       if (tid == 0) atomicExch(a.status + ST_TIMEOUT, 1);
       return;
     }
@@ -1595,9 +1597,9 @@ static bool shape_for(SolveArgsT<CT>& a, const SolveCfg& c, int* threads, size_t
     const size_t fac = ((fwdb > bwdb ? fwdb : bwdb) + 127) & ~(size_t)127;
     const size_t stage_bytes = (fac + 2 * (size_t)16 * c.nc * sizeof(CT) + 127) & ~(size_t)127;
     const size_t budget = 210 * 1024;
-    int nstage = c.stages > 4 ? c.stages : 4;
+    int nstage = c.stages > 3 ? c.stages : 3;
     auto need = [&](int k) { return ((4 * (size_t)k * 8 + 127) & ~(size_t)127) + k * stage_bytes; };
-    while (nstage > 4 && need(nstage) > budget) --nstage;
+    while (nstage > 3 && need(nstage) > budget) --nstage;
     if (need(nstage) > budget) return false;
     a.nstage = nstage;
     *smem = need(nstage);
@@ -1736,9 +1738,11 @@ static cudaError_t launch_tuned(const SolveArgsT<CT>& a, int q, cudaStream_t s) 
         c.push_back({8, spt0, 4, 1});
         c.push_back({8, 2, 3, 1});
       }
-      // its look-ahead form
+      // its look-ahead form (as many stages as fit, at least three; the second shape with
+      // exactly three)
       c.push_back({4, spt0, 6, 2});
       c.push_back({4, 2, 6, 2});
+      c.push_back({4, 2, 3, 2});
       c.push_back({2, spt0, 6, 2});
       c.push_back({2, 2, 6, 2});
       if (fp32) {
