@@ -35,13 +35,15 @@ MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 HBM_FALLBACK_GBS = 6800.0
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12     # 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # 152 SMs x 128 FP32 FMA/clk x 2 flop x 2.07 GHz
-# DRAM traffic of one complex128 band_solve_kernel launch per algorithmic byte, from the ncu
-# capture at p1_m160 (profiles/band_solve_blocked_c128_p1_m160.md, the current kernel):
-# dram__bytes_read.sum + dram__bytes_write.sum = 1.933231e9 + 0.399216e9 B against 2.231832e9
-# algorithmic bytes. The traffic is the factors (q n (kl + kv) entries, once) plus the blocks,
-# so it scales with the algorithmic bytes; the bench workload's traffic is this ratio times its
-# algorithmic bytes.
-C128_SOLVE_TRAFFIC_RATIO = (1.933231e9 + 0.399216e9) / 2.231832e9
+# DRAM traffic of one complex128 band-solve launch per algorithmic byte, by kernel, from ncu
+# captures at p1_m160 (profiles/band_solve_blocked_c128_p1_m160.md and
+# profiles/band_solve_la_c128_p1_m160.md): dram__bytes_read.sum + dram__bytes_write.sum against
+# 2.231832e9 algorithmic bytes per launch. The traffic is the factors (q n (kl + kv) entries,
+# once) plus the blocks, so it scales with the algorithmic bytes; the bench workload's traffic
+# is this ratio times its algorithmic bytes. A kernel without a capture reports no traffic.
+SOLVE_KERNELS = {0: "band_solve_kernel", 1: "band_solve_pipe_kernel", 2: "band_solve_la_kernel"}
+C128_SOLVE_TRAFFIC_RATIO = {0: (1.933231e9 + 0.399216e9) / 2.231832e9,
+                            2: (1.935151e9 + 0.399184e9) / 2.231832e9}
 
 
 def parse():
@@ -259,6 +261,8 @@ def run_native(args):
     t_ms = ev0.elapsed_time(ev1)
     _, sB = ie.ie_get_stats(h)
     t_ms = max_over_ranks(t_ms, dist, device)
+    # the kernel family the launch-shape tuner settled on for the timed solves
+    solve_kernel = sB["solve_kernel"] if args.precision == 0 else sB["solve32_kernel"]
     if args.precision == 0:
         launches = sB["solve_launches"] - sA["solve_launches"]
         solve_ms = sB["t_solve_ms"] - sA["t_solve_ms"]
@@ -392,20 +396,21 @@ def run_native(args):
         alg_bytes = solve_by / launches if (launches and solve_by) else None
         avg_ms = solve_ms / launches if launches else None
         hbm_gbs = alg_bytes / (avg_ms / 1e3) / 1e9 if (alg_bytes and avg_ms) else None
+        ratio = C128_SOLVE_TRAFFIC_RATIO.get(solve_kernel) if args.precision == 0 else None
         roofline = {
             "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
             "frac": achieved / peak if achieved else None,
-            "traffic": (C128_SOLVE_TRAFFIC_RATIO * alg_bytes
-                        if (args.precision == 0 and alg_bytes) else None),
-            "kernel": "band_solve_kernel (%s complex band solves)"
-                      % ("FP64" if args.precision == 0 else "FP32"),
+            "traffic": ratio * alg_bytes if (ratio and alg_bytes) else None,
+            "kernel": "%s (%s complex band solves, the tuner's choice)"
+                      % (SOLVE_KERNELS.get(solve_kernel, "band solve"),
+                         "FP64" if args.precision == 0 else "FP32"),
             "peak_source": ("derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz "
                             "(measured FP64 FMA probe: 1.20 TFLOP/s)")
                            if args.precision == 0 else
                            ("derived: 152 SMs x 128 FP32 FMA/clk x 2 flop x 2.07 GHz "
                             "(measured FP32 FMA probe: 70.2 TFLOP/s)"),
             "traffic_source": ("ncu capture at p1_m160 scaled by algorithmic bytes"
-                               if args.precision == 0 else None),
+                               if ratio else None),
             "algorithmic_bytes_per_launch": alg_bytes,
             "algorithmic_flops_per_launch": solve_fl / launches if launches else None,
             "launches": launches, "avg_launch_ms": avg_ms,

@@ -121,6 +121,10 @@ typedef struct {
   int64_t refine_solves;   /* precision = 1: FP32 refinement solves (each: q poles x the block) since create */
   double refine_last_corr; /* precision = 1: the last refinement step's largest relative correction
                               max |dx|_inf / |x|_inf over poles and columns (an error estimate) */
+  int32_t solve_kernel;    /* band-solve kernel of the last complex128 solve launched in this
+                              process: 0 barrier-synchronised, 1 warp-specialised, 2 look-ahead
+                              (the launch-shape tuner's choice); -1 none yet */
+  int32_t solve32_kernel;  /* the same for the complex64 solves */
 } ie_stats;
 
 /* ie_create: computes the inner poles/weights (Eq. pwtp, q points) and the outer

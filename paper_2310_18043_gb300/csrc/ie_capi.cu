@@ -1812,6 +1812,8 @@ static void fill_solve_stats(ie_handle h, ie_stats* out) {
   out->adj_flops = h->adj_flops;
   out->refine_solves = h->refine_solves;
   out->refine_last_corr = h->refine_last_corr;
+  out->solve_kernel = band_solve_last_kernel(0);
+  out->solve32_kernel = band_solve_last_kernel(1);
 }
 
 extern "C" ie_status ie_get_stats(ie_handle h, ie_stats* out) {

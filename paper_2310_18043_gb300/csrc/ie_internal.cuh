@@ -160,6 +160,9 @@ void launch_block_transforms(int q, int64_t n, int64_t n_pad, int kl, int ldab, 
 void launch_block_transforms(int q, int64_t n, int64_t n_pad, int kl, int ldab, const float2* AB,
                              const int* piv, const float2* dinv, int* H, float2* T32,
                              float2* Ui32, cudaStream_t s);
+// kernel family of the last tuned band-solve launch in this process (fp32 = 0: complex128,
+// 1: complex64): 0 barrier-synchronised, 1 warp-specialised, 2 look-ahead; -1 none yet
+int band_solve_last_kernel(int fp32);
 // Mixed precision: complex64 band solves; X (FP64, per pole) = x (accumulate = 0), or
 // (accumulate = 1) x is written in place over the forward result in Y32 and X is untouched.
 // RHS column c of pole i at RHS + i*rstride + c*ldr (rstride 0: shared right-hand side).

@@ -15,6 +15,7 @@
 // time into a shared ring by cp.async.bulk (TMA bulk copies) with mbarrier completion; every
 // wait is bounded.
 #include <algorithm>
+#include <atomic>
 #include <cstdio>
 #include <cstdlib>
 #include <map>
@@ -1704,6 +1705,11 @@ bool tune_log() {
 }
 }  // namespace
 
+namespace {
+std::atomic<int> g_last_kernel[2] = {-1, -1};
+}  // namespace
+int band_solve_last_kernel(int fp32) { return g_last_kernel[fp32 ? 1 : 0].load(); }
+
 template <typename CT>
 static cudaError_t launch_tuned(const SolveArgsT<CT>& a, int q, cudaStream_t s) {
   int dev = 0, sms = 0;
@@ -1712,7 +1718,10 @@ static cudaError_t launch_tuned(const SolveArgsT<CT>& a, int q, cudaStream_t s) 
   const bool fp32 = sizeof(CT) == sizeof(float2);
   const int spt0 = ((a.kv > NB ? a.kv : NB) > 576) ? 2 : 1;
   const SolveCfg dflt{pick_nc(q, a.k, sms, fp32 ? 8 : 4), spt0, 6, 0};
-  if (!tune_enabled()) return launch_cfg(a, q, dflt, s);
+  if (!tune_enabled()) {
+    g_last_kernel[fp32 ? 1 : 0] = dflt.pipe;
+    return launch_cfg(a, q, dflt, s);
+  }
   int kb = 1;
   while (kb < a.k) kb *= 2;
   const TuneKey key{(int)sizeof(CT), a.kl, q, kb};
@@ -1796,6 +1805,7 @@ static cudaError_t launch_tuned(const SolveArgsT<CT>& a, int q, cudaStream_t s) 
     if (slot >= 0) cudaEventRecord(T.e0[slot], s);
   }
   cudaError_t e = launch_cfg(a, q, use, s);
+  g_last_kernel[fp32 ? 1 : 0] = e == cudaSuccess ? use.pipe : dflt.pipe;
   if (slot >= 0) {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     TuneState& T = g_tune[key];

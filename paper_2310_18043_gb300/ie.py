@@ -52,7 +52,8 @@ class ie_stats(C.Structure):
                 ("solve32_launches", C.c_int64), ("t_solve32_ms", C.c_double),
                 ("solve32_flops", C.c_double), ("adj_launches", C.c_int64),
                 ("t_adj_ms", C.c_double), ("adj_flops", C.c_double),
-                ("refine_solves", C.c_int64), ("refine_last_corr", C.c_double)]
+                ("refine_solves", C.c_int64), ("refine_last_corr", C.c_double),
+                ("solve_kernel", C.c_int32), ("solve32_kernel", C.c_int32)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
