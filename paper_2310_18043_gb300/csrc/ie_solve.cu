@@ -953,12 +953,12 @@ __global__ void __maxnreg__(REGS) band_solve_pipe_kernel(SolveArgsT<CT> a) {
 // previous use G+2-ns was last read by head G+2-ns (IN) and head G+3-ns (factors and OUT of
 // the catch-up), both before head G for ns >= 3, and the update warps still reading OUT(G-1)
 // for ns = 3 touch another part of the stage. Every wait is bounded.
-template <typename CT, int NC, int SPT, int REGS>
-__global__ void __maxnreg__(REGS) band_solve_la_kernel(SolveArgsT<CT> a) {
+// One CTA's work: pole `pole`, right-hand sides grp*NC .. grp*NC+NC-1 of the solve `a`.
+template <typename CT, int NC, int SPT>
+__device__ __forceinline__ void la_cta(const SolveArgsT<CT>& a, const int pole, const int grp) {
   constexpr int HC = NC >= 2 ? 2 : 1;          // right-hand sides per head warp
   constexpr int NH = NC / HC;                  // head warps
-  const int pole = blockIdx.y;
-  const int c0 = blockIdx.x * NC;
+  const int c0 = grp * NC;
   const int ncol = min(NC, a.k - c0);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int WU = (int)(blockDim.x >> 5) - NH - 1;   // update warps
@@ -1395,6 +1395,23 @@ __global__ void __maxnreg__(REGS) band_solve_la_kernel(SolveArgsT<CT> a) {
       if (lane == 0) mbar_arrive(EMPTY(s));
     }
   }
+}
+
+template <typename CT, int NC, int SPT, int REGS>
+__global__ void __maxnreg__(REGS) band_solve_la_kernel(SolveArgsT<CT> a) {
+  la_cta<CT, NC, SPT>(a, blockIdx.y, blockIdx.x);
+}
+
+// The look-ahead solve of many independent problems in one launch, laid out as
+// band_solve_batch_kernel: CTA b serves solve cta[b].x, pole cta[b].y, column group cta[b].z;
+// the block size is that of the widest band (a narrower solve leaves the extra update slots
+// idle) and each solve has its own staged-panel count.
+template <typename CT, int NC, int SPT, int REGS>
+__global__ void __maxnreg__(REGS) band_solve_la_batch_kernel(const SolveArgsT<CT>* items,
+                                                             const int4* cta) {
+  const int4 m = cta[blockIdx.x];
+  const SolveArgsT<CT> a = items[m.x];
+  la_cta<CT, NC, SPT>(a, m.y, m.z);
 }
 
 // ----------------------------------------------------------------------------------------------
@@ -1979,10 +1996,109 @@ static cudaError_t batch_launch_r(BandSolveBatch* b, std::vector<SolveArgsT<CT>>
   return cudaGetLastError();
 }
 
+template <typename CT, int SPT, int REGS>
+static cudaError_t batch_la_launch_r(BandSolveBatch* b, std::vector<SolveArgsT<CT>>& items,
+                                     int threads, size_t smem, cudaStream_t s) {
+  auto kfn = band_solve_la_batch_kernel<CT, 4, SPT, REGS>;
+  cudaError_t e = ie_smem_optin((const void*)kfn);
+  if (e != cudaSuccess) return e;
+  int blocks = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, kfn, threads, smem);
+  if (e != cudaSuccess) return e;
+  if (blocks < 1) return cudaErrorLaunchOutOfResources;
+  const size_t ib = items.size() * sizeof(SolveArgsT<CT>);
+  if (ib > b->items_cap) {
+    cudaFree(b->d_items);
+    b->d_items = nullptr;
+    e = cudaMalloc(&b->d_items, ib);
+    if (e != cudaSuccess) { b->items_cap = 0; return e; }
+    b->items_cap = ib;
+  }
+  if (b->cta.size() > b->cta_cap) {
+    cudaFree(b->d_cta);
+    b->d_cta = nullptr;
+    e = cudaMalloc(&b->d_cta, b->cta.size() * sizeof(int4));
+    if (e != cudaSuccess) { b->cta_cap = 0; return e; }
+    b->cta_cap = b->cta.size();
+  }
+  // pageable sources: the copies complete before cudaMemcpyAsync returns to the host
+  e = cudaMemcpyAsync(b->d_items, items.data(), ib, cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) return e;
+  e = cudaMemcpyAsync(b->d_cta, b->cta.data(), b->cta.size() * sizeof(int4),
+                      cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) return e;
+  kfn<<<(unsigned)b->cta.size(), threads, smem, s>>>((const SolveArgsT<CT>*)b->d_items, b->d_cta);
+  ie_count_launch();
+  return cudaGetLastError();
+}
+
+// The batch as one look-ahead launch (4 right-hand sides per CTA, two window slots per thread
+// above 256 slots): each solve gets the staged panels that fit the common shared-memory size,
+// at least three. Returns cudaErrorInvalidValue when some solve does not fit (the caller then
+// uses the synchronised batch kernel).
+template <typename CT>
+static cudaError_t batch_la_launch_t(BandSolveBatch* b, std::vector<SolveArgsT<CT>>& items,
+                                     const std::vector<int>& qs, cudaStream_t s) {
+  constexpr int NCB = 4, NHB = 2;
+  int slots = 2 * NB;
+  for (auto& a : items) slots = std::max(slots, a.kv);
+  const int spt = slots > 256 ? 2 : 1;
+  const int wu = ((slots + spt - 1) / spt + 31) / 32;
+  const int threads = (wu + NHB + 1) * 32;
+  if (threads > 640) return cudaErrorInvalidValue;
+  const size_t budget = 210 * 1024;
+  auto stage_of = [&](const SolveArgsT<CT>& a) {
+    const size_t fwdb = (size_t)NB * a.klp * sizeof(CT) + 256 * sizeof(CT) + 32 * sizeof(int);
+    const size_t bwdb = (size_t)NB * a.kvp * sizeof(CT) + 64 * sizeof(CT);
+    const size_t fac = ((fwdb > bwdb ? fwdb : bwdb) + 127) & ~(size_t)127;
+    return (fac + 2 * (size_t)16 * NCB * sizeof(CT) + 127) & ~(size_t)127;
+  };
+  auto need = [&](int k, size_t st) { return ((4 * (size_t)k * 8 + 127) & ~(size_t)127) + k * st; };
+  size_t smem = 0;
+  for (auto& a : items) {
+    const size_t st = stage_of(a);
+    if (need(3, st) > budget) return cudaErrorInvalidValue;
+    int ns = 3;
+    while (ns < 6 && need(ns + 1, st) <= budget) ++ns;
+    a.nstage = ns;
+    smem = std::max(smem, need(ns, st));
+  }
+  std::vector<int> ord(items.size());
+  for (size_t i = 0; i < ord.size(); ++i) ord[i] = (int)i;
+  std::stable_sort(ord.begin(), ord.end(), [&](int x, int y) {
+    return items[x].n * (items[x].kl + items[x].kv) > items[y].n * (items[y].kl + items[y].kv);
+  });
+  b->cta.clear();
+  for (int i : ord)
+    for (int p = 0; p < qs[i]; ++p)
+      for (int g = 0; g * NCB < items[i].k; ++g) b->cta.push_back(make_int4(i, p, g, 0));
+  const int wps = (threads / 32 + 3) / 4;
+  if (spt == 1) {
+    if (wps <= 3) return batch_la_launch_r<CT, 1, 168>(b, items, threads, smem, s);
+    if (wps <= 4) return batch_la_launch_r<CT, 1, 128>(b, items, threads, smem, s);
+    if (wps <= 5) return batch_la_launch_r<CT, 1, 96>(b, items, threads, smem, s);
+    return cudaErrorInvalidValue;
+  }
+  if (wps <= 3) return batch_la_launch_r<CT, 2, 168>(b, items, threads, smem, s);
+  if (wps <= 4) return batch_la_launch_r<CT, 2, 128>(b, items, threads, smem, s);
+  if (wps <= 5) return batch_la_launch_r<CT, 2, 96>(b, items, threads, smem, s);
+  return cudaErrorInvalidValue;
+}
+
 template <typename CT>
 static cudaError_t batch_launch_t(BandSolveBatch* b, std::vector<SolveArgsT<CT>>& items,
                                   const std::vector<int>& qs, cudaStream_t s) {
   if (items.empty()) return cudaSuccess;
+  // the look-ahead kernel when every solve fits it (IE_BATCH_SYNC=1: always the synchronised one)
+  static const bool force_sync = [] {
+    const char* e = getenv("IE_BATCH_SYNC");
+    return e && e[0] == '1';
+  }();
+  if (!force_sync) {
+    std::vector<SolveArgsT<CT>> la = items;
+    const cudaError_t e = batch_la_launch_t(b, la, qs, s);
+    if (e != cudaErrorInvalidValue) return e;
+  }
   constexpr int NCB = 4;
   int slots = NB;
   for (auto& a : items) slots = std::max(slots, a.kv);
