@@ -1,4 +1,6 @@
-"""CPU emulation of the look-ahead band-solve protocol (`band_solve_la_kernel`).
+"""CPU emulations of the band-solve kernels' orders: the look-ahead protocol
+(`band_solve_la_kernel`) and the synchronised one (`band_solve_kernel`,
+`band_solve_pipe_kernel`).
 
 The kernel splits each sweep of the blocked band solve (Sec. 3.2, the inner operator's
 K_i^{-1}: P, L forward, U backward, in LAPACK gbtrs order) into head warps and update warps
@@ -253,3 +255,78 @@ def test_emulation_detects_a_missing_delivery():
     exec(code.replace("elif m >= NB and H2[m] == r + Sf:", "elif False:"), g)
     with pytest.raises(AssertionError):
         g["_look_ahead_solve"](n, kl, lu, piv, b)
+
+
+def _synchronised_solve(n, kl, lu, piv, b):
+    """The barrier-synchronised kernels' order (`band_solve_kernel`, `band_solve_pipe_kernel`):
+    per panel the head (T H forward, inv(U_block) h backward), then the window update, whose
+    first NB rows become the next head; the window holds max(kl, NB) / max(kv, NB) rows."""
+    kv = 2 * kl
+    npan = (n + NB - 1) // NB
+    n_pad = npan * NB
+    pans, L, U = _panels(n, kl, lu, piv)
+    R = lambda r: b[r] if 0 <= r < n else 0
+    Sf = max(kl, NB)
+    hd = [R(t) for t in range(NB)]
+    frow = [NB + s for s in range(Sf)]
+    v = [R(r) for r in frow]
+    y = np.zeros(n, complex)
+    for P in range(npan):
+        H, T, _ = pans[P]
+        j0, nvalid = P * NB, min(n - P * NB, NB)
+        hv = np.zeros(16, complex)
+        hv[:NB] = hd
+        mem = [-1] * Sf
+        for s in range(Sf):
+            if frow[s] in H[NB:]:
+                mem[s] = H.index(frow[s])
+                hv[mem[s]] = v[s]
+        out = np.array([T[i] @ hv if H[i] >= 0 else 0 for i in range(16)])
+        y[j0:j0 + nvalid] = out[:nvalid]
+        for s in range(Sf):
+            r = frow[s]
+            if mem[s] >= NB:
+                v[s] = out[mem[s]]
+            else:
+                for jj in range(nvalid):
+                    if r - (j0 + jj) <= kl:
+                        v[s] -= L(r, j0 + jj) * out[jj]
+            if r - j0 - NB < NB:
+                hd[r - j0 - NB] = v[s]
+                frow[s] = r + Sf
+                v[s] = R(r + Sf)
+    Sb = max(kv, NB)
+    Y = lambda r: y[r] if 0 <= r < n else 0
+    top = n_pad - 1
+    hd = [Y(top - t) for t in range(NB)]
+    row = [top - NB - s for s in range(Sb)]
+    v = [Y(r) for r in row]
+    x = np.zeros(n, complex)
+    for Bp in range(npan):
+        j0 = top - Bp * NB
+        Ui = pans[(j0 - NB + 1) // NB][2]
+        xs = np.array([Ui[NB - 1 - t, ::-1] @ np.array(hd) for t in range(NB)])
+        for t in range(NB):
+            if j0 - t < n:
+                x[j0 - t] = xs[t]
+        for s in range(Sb):
+            r = row[s]
+            base = j0 - r
+            for s2 in range(NB):
+                if base - s2 <= kv:
+                    v[s] -= U(r, j0 - s2) * xs[s2]
+            if base - NB < NB:
+                hd[base - NB] = v[s]
+                row[s] = r - Sb
+                v[s] = Y(r - Sb)
+    return x
+
+
+@pytest.mark.parametrize("n,kl,seed", [(37, 3, 0), (64, 1, 1), (50, 5, 2), (83, 11, 3),
+                                        (20, 12, 4), (17, 2, 5), (16, 0, 12)])
+def test_synchronised_order_solves_the_factored_matrix(n, kl, seed):
+    K, lu, piv = _band_factor(n, kl, seed)
+    b = np.random.default_rng(9).standard_normal(n) + 1j
+    x = _synchronised_solve(n, kl, lu, piv, b)
+    ref = np.linalg.solve(K, b)
+    assert np.linalg.norm(x - ref) / np.linalg.norm(ref) < 1e-12
